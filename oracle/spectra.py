@@ -1,0 +1,71 @@
+"""Shell energy spectra and scalar diagnostics, FP64 numpy (Sec. 4.3, 5).
+
+TEST INFRASTRUCTURE (see ``oracle/__init__.py``).
+
+Conventions (the paper normalises spectra by the total energy but does not
+fix the binning):
+  u_hat(m) = N^-3 sum_x u(x) exp(-i k.x), k = 2 pi m / N per axis;
+  shell n = round(|m|);  E(n) = 1/2 sum_{shell n} |u_hat|^2, so that the sum
+  over every shell is 1/2 <|u|^2> (Parseval).
+Scalars: E_u = 1/2 <|u|^2>, E_B = 1/2 <|B - <B>|^2>, H_c = <u.(B - <B>)>,
+<|J|^2>, enstrophy <|curl u|^2> (spectral curl), mass, momentum, <B>.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _wavenumbers(shape):
+    nz, ny, nx = shape
+    mz = np.fft.fftfreq(nz, 1.0 / nz)[:, None, None]
+    my = np.fft.fftfreq(ny, 1.0 / ny)[None, :, None]
+    mx = np.fft.fftfreq(nx, 1.0 / nx)[None, None, :]
+    return mx, my, mz
+
+
+def shell_index(shape):
+    mx, my, mz = _wavenumbers(shape)
+    return np.rint(np.sqrt(mx * mx + my * my + mz * mz)).astype(np.int64)
+
+
+def shell_spectrum(F, nshell):
+    """E(n), n < nshell, of a real vector field F [3, nz, ny, nx]."""
+    shape = F.shape[1:]
+    n3 = float(np.prod(shape))
+    p = np.zeros(shape)
+    for c in range(F.shape[0]):
+        fh = np.fft.fftn(F[c]) / n3
+        p += np.abs(fh) ** 2
+    idx = shell_index(shape).ravel()
+    keep = idx < nshell
+    return 0.5 * np.bincount(idx[keep], weights=p.ravel()[keep], minlength=nshell)[:nshell]
+
+
+def enstrophy(u):
+    """<|curl u|^2> by the spectral curl (k = 2 pi m / N)."""
+    shape = u.shape[1:]
+    n3 = float(np.prod(shape))
+    mx, my, mz = _wavenumbers(shape)
+    kx, ky, kz = (2 * np.pi * mx / shape[2], 2 * np.pi * my / shape[1], 2 * np.pi * mz / shape[0])
+    uh = [np.fft.fftn(u[c]) / n3 for c in range(3)]
+    wx = 1j * (ky * uh[2] - kz * uh[1])
+    wy = 1j * (kz * uh[0] - kx * uh[2])
+    wz = 1j * (kx * uh[1] - ky * uh[0])
+    return float(np.sum(np.abs(wx) ** 2 + np.abs(wy) ** 2 + np.abs(wz) ** 2))
+
+
+def scalars(rho, u, B, J):
+    """Scalar diagnostics as a dict (FP64)."""
+    Bm = B.reshape(3, -1).mean(axis=1)
+    b = B - Bm[:, None, None, None]
+    return dict(
+        mass=float(rho.sum()),
+        momentum=[float((rho * u[a]).sum()) for a in range(3)],
+        B_mean=[float(v) for v in Bm],
+        E_u=0.5 * float((u * u).sum(axis=0).mean()),
+        E_B=0.5 * float((b * b).sum(axis=0).mean()),
+        H_c=float((u * b).sum(axis=0).mean()),
+        J2=float((J * J).sum(axis=0).mean()),
+        enstrophy=enstrophy(u),
+        u_max=float(np.sqrt((u * u).sum(axis=0)).max()),
+    )
