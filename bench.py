@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Throughput of the fused FLAME Hall-MHD lattice-Boltzmann step on GB300.
+
+Workload (default): 256^3 decaying Hall-MHD turbulence -- seeded random-phase
+solenoidal u and B with energy in shells 1..4 (u_rms = b_rms = 0.05, seeds 3
+and 4), rho = 1, tau_nu = tau_eta = 0.51, d_i = 0.05 * 256 = 12.8.  The
+headline is FP16 deviation storage with FP32 collision; FP32 and BF16
+storage are timed in the same run.  A step is one launch of the fused
+collide-and-stream kernel over all 256^3 sites.
+
+Metric: MLUPS (million lattice-site updates per second) and the fraction of
+the measured HBM bandwidth reached by the step kernel, with the per-field
+and per-shell error of the reduced-precision runs against the FP32 run.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--n 256] [--impl flame|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (weak scaling, no data-path collective); the value
+is the sum of all ranks' site updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline at 256^3 (FP32 vs FP16-storage) at stated L2 error"
+BYTES_PER_SITE = {"fp32": 48 * 4 * 2, "fp16": 48 * 2 * 2, "bf16": 48 * 2 * 2}  # AA in place: read + write 48
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0
+L2_BYTES = 129 * 2 ** 20
+
+
+def workload(n):
+    return dict(tau_nu=0.51, tau_eta=0.51, d_i=0.05 * n, rms=0.05, shells=(1, 4), seed_u=3, seed_b=4)
+
+
+def workload_name(n, storage):
+    w = workload(n)
+    return (f"{n}^3 decaying Hall-MHD turbulence: seeded random-phase solenoidal u, B in shells 1-4, "
+            f"u_rms=b_rms={w['rms']}, rho=1, tau_nu=tau_eta={w['tau_nu']}, d_i={w['d_i']:g}; "
+            f"{storage.upper()} deviation storage, FP32 collision")
+
+
+# --------------------------------------------------------------------------- helpers
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("step.cu", "lattice.cuh", "flame_internal.h"):
+        with open(os.path.join(ROOT, "paper_2212_11024_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(storage):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_256.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"traffic_bytes_per_launch_{storage}:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in a background thread."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.windows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def window(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        inside = [s for t, s in self.samples if any(a <= t <= b for a, b in self.windows)]
+        use = inside if inside else [s for _, s in self.samples]
+        if not use:
+            return None
+        sm = [float(s[1]) for s in use if s[1].replace(".", "", 1).isdigit()]
+        mx = [float(s[2]) for s in use if s[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in use for i in range(4) if len(s) > 5 + i and s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
+
+
+# --------------------------------------------------------------------------- oracle timing
+def oracle_mlups(n, steps, threads=0):
+    """Time `steps` oracle steps (literal 27x27 mode, FP64, OpenMP) on an n^3
+    instance of the workload recipe; returns (MLUPS, seconds, cores)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2212_11024_gb300 import inputs
+
+    w = workload(n)
+    cores = O.threads(threads)
+    u, B = inputs.turbulence((n, n, n), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
+    p = O.Params(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"])
+    pop = O.init(p, None, u, B)
+    del u, B
+    scratch = np.empty_like(pop)
+    t0 = time.perf_counter()
+    O.step(p, pop, steps, literal=True, scratch=scratch)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt / 1e6, dt, cores
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, in the arm's metric and unit.
+    Each timed step is one oracle step on an n^3 instance of the workload recipe,
+    n chosen so that the whole run takes about two minutes."""
+    import oracle as O
+
+    O.build()
+    rate, _, _ = oracle_mlups(16, 2)  # calibration
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = int((budget * rate * 1e6) ** (1.0 / 3.0))
+    n = max(10, min(args.n, n - n % 2))
+    import numpy as np
+
+    from paper_2212_11024_gb300 import inputs
+
+    w = workload(n)
+    cores = O.threads(0)
+    u, B = inputs.turbulence((n, n, n), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
+    p = O.Params(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"])
+    pop = O.init(p, None, u, B)
+    scratch = np.empty_like(pop)
+    for _ in range(args.warmup):
+        O.step(p, pop, 1, literal=True, scratch=scratch)
+    t0 = time.perf_counter()
+    O.step(p, pop, args.steps, literal=True, scratch=scratch)
+    dt = time.perf_counter() - t0
+    val = n ** 3 * args.steps / dt / 1e6
+    sample = (f"{n}^3 periodic instance of the workload recipe (d_i = 0.05 n), one FP64 oracle step "
+              f"(literal 27x27 central-moment inversion) per timed step")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.n, "fp16"), "n": args.n, "sample_n": n,
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--impl", default="flame", choices=["flame", "reference"])
+    ap.add_argument("--storage", default="fp16,fp32,bf16", help="first entry is the headline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2212_11024_gb300 import Flame, FlameError, build as B, inputs
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    w = workload(n)
+    u_h, B_h = inputs.turbulence((n, n, n), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
+    u_d = torch.from_numpy(u_h).to(dev)
+    B_d = torch.from_numpy(B_h).to(dev)
+    storages = [s.strip() for s in args.storage.split(",") if s.strip()]
+    head = storages[0]
+    peak, peak_src = hbm_peak()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream(dev)
+    variants, finals = {}, {}
+    for st in storages:
+        sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev)
+        sim.init(None, u_d, B_d)
+        sim.step(args.warmup)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_wall0 = time.time()
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        t_wall1 = time.time()
+        barrier()
+        clocks.window(t_wall0, t_wall1)
+        ms = e0.elapsed_time(e1)
+        ms_max = max_over_ranks(ms)
+        status = "ok"
+        try:
+            sim.sync()
+        except FlameError as ex:
+            status = f"nonfinite ({ex.status})"
+        sites = n ** 3
+        mlups = world * sites * args.steps / (ms_max * 1e-3) / 1e6
+        per_launch_s = ms / args.steps * 1e-3
+        achieved = BYTES_PER_SITE[st] * sites / per_launch_s / 1e9
+        variants[st] = {"mlups": mlups, "ms_per_step": ms_max / args.steps, "achieved_gbs": achieved,
+                        "frac_of_measured_hbm": achieved / peak, "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                        "algorithmic_bytes_per_site": BYTES_PER_SITE[st], "state_gb": 48 * sites * (4 if st == "fp32" else 2) / 1e9,
+                        "status": status}
+        m = sim.moments(out={"u": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
+                             "B": torch.empty((3, n, n, n), dtype=torch.float64, device=dev)})
+        Eu, Eb = sim.spectra(n // 2 + 1)
+        finals[st] = (m["u"], m["B"], Eu, Eb)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+
+    # accuracy of the reduced-storage runs against the FP32 run (same input, same steps)
+    accuracy = {}
+    if "fp32" in finals:
+        ru, rb, rEu, rEb = finals["fp32"]
+        shells = np.arange(1, n // 4 + 1)
+        for st in storages:
+            if st == "fp32":
+                continue
+            gu, gb, gEu, gEb = finals[st]
+            accuracy[st] = {
+                "rel_l2_u": float(torch.linalg.vector_norm(gu - ru) / torch.linalg.vector_norm(ru)),
+                "rel_l2_B": float(torch.linalg.vector_norm(gb - rb) / torch.linalg.vector_norm(rb)),
+                "max_shell_rel_err_Eu_n1_to_N4": float(np.max(np.abs(gEu[shells] - rEu[shells]) / rEu[shells])),
+                "max_shell_rel_err_Eb_n1_to_N4": float(np.max(np.abs(gEb[shells] - rEb[shells]) / rEb[shells])),
+                "reference": f"FP32 storage run, same input, after {args.warmup + args.steps} steps",
+            }
+    finals.clear()
+
+    # end to end through the public API with host buffers: H2D of the initial
+    # fields, flame_init, K steps, D2H of u, B, J and the FP64 scalars.
+    pin_u = torch.from_numpy(u_h).pin_memory()
+    pin_B = torch.from_numpy(B_h).pin_memory()
+    out_h = torch.empty((9, n, n, n), dtype=torch.float64).pin_memory()
+    sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=head, device=dev)
+    outs = {"u": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
+            "B": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
+            "J": torch.empty((3, n, n, n), dtype=torch.float64, device=dev)}
+    barrier()
+    t0 = time.perf_counter()
+    u_d.copy_(pin_u, non_blocking=True)
+    B_d.copy_(pin_B, non_blocking=True)
+    sim.init(None, u_d, B_d)
+    sim.step(args.steps)
+    sim.moments(out=outs)
+    out_h[0:3].copy_(outs["u"], non_blocking=True)
+    out_h[3:6].copy_(outs["B"], non_blocking=True)
+    out_h[6:9].copy_(outs["J"], non_blocking=True)
+    scal = sim.reduce()
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    sim.close()
+    h2d = 2 * 3 * n ** 3 * 8
+    d2h = 9 * n ** 3 * 8 + 14 * 8
+    e2e = {"value": world * n ** 3 * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "job": "pinned host u,B -> device, flame_init, K x flame_step, flame_moments u,B,J -> pinned host, "
+                  "flame_reduce scalars", "seconds": e2e_s, "gpu_launches": 1 + args.steps + 1 + 2,
+           "final_E_u": scal["E_u"], "final_E_B": scal["E_B"]}
+    clk = clocks.stop()
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        val, secs, cores = oracle_mlups(n, 1)
+        cpu = {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"one FP64 oracle step (literal 27x27 central-moment inversion) of the {n}^3 workload, "
+                         f"{secs:.1f} s on {cores} threads"}
+
+    hv = variants[head]
+    traffic = recorded_traffic(head)
+    line = {
+        "metric": METRIC, "value": hv["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": hv["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(n, head), "n": n, "storage": head, "compute": "fp32",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"no flush: the {hv['state_gb']:.2f} GB state streamed each step exceeds the 129 MB L2"},
+        "roofline": {"bound": "hbm", "achieved": hv["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": hv["achieved_gbs"] / peak, "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": hv["algorithmic_bytes_per_site"] * n ** 3,
+                     "kernel": f"step_kernel<{head}> (fused collide + AA stream)",
+                     "frac_of_nominal_8tbs": hv["achieved_gbs"] / NOMINAL_HBM_GBS,
+                     "kernel_source_sha256_16": kernel_source_hash()},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
+        "variants": variants, "accuracy": accuracy,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

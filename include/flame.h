@@ -1,0 +1,186 @@
+/*
+ * flame.h -- C ABI of the GB300 implementation of one fused lattice-Boltzmann
+ * time step for 3-D periodic Hall-MHD (the FLAME scheme of Foldes et al.,
+ * arXiv 2212.11024: D3Q27 central-moment fluid, Sec. 3.1, plus three D3Q7 BGK
+ * magnetic populations with the Hall term in their equilibrium, Sec. 3.2).
+ *
+ * Problem statement (Sec. 3.3, 4.1, 5): given a periodic nx x ny x nz lattice,
+ * the lattice viscosity and resistivity (through the relaxation times), the
+ * Hall length d_i and initial rho, u, B, advance n time steps and return u,
+ * B, J, energies and spectra.  Everything is in lattice units
+ * (dx = dt = 1, c_s^2 = 1/3, C^2 = 1/4, alpha_H = d_i).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers, h_* host pointers.  The caller
+ *    owns all of them, including the population state; the library never
+ *    frees caller memory.  The library owns the context and, after the first
+ *    flame_reduce / flame_spectra call, an internal device workspace that
+ *    flame_destroy releases.
+ *  - Work is queued asynchronously on the stream given to flame_create.
+ *    Calls that return host data (flame_reduce, flame_spectra, flame_sync,
+ *    flame_init) synchronise that stream.
+ *  - Errors are returned as flame_status; nothing throws across the ABI.  A
+ *    CUDA error, or a non-finite value seen by the step kernel, is sticky:
+ *    every later call on the context returns it.  Asynchronous CUDA errors
+ *    surface at the next synchronising call.
+ *  - Fields are structure-of-arrays [component][z][y][x], x fastest, with
+ *    N3 = nx*ny*nz sites per component.  Gradients are [3a+b][z][y][x] for
+ *    d_a F_b.
+ *
+ * Population state (flame_state_bytes bytes, 256-byte aligned): 48 slots of
+ * N3 values.  Slot q = 0..26 holds the fluid population on App. A's D3Q27
+ * velocity q; slot 27 + 7b + i the magnetic component b (x, y, z) on D3Q7
+ * velocity i (rest, +x, -x, +y, -y, +z, -z).  The state is updated in place
+ * with the AA access pattern, so which site and slot hold a given population
+ * depends on the step parity (flame_info).  A slot stores the population's
+ * deviation from the rest equilibrium of the reference state (rho0, B_ref)
+ * divided by its lattice weight, as FP32, FP16 or BF16 (round to nearest even).
+ */
+#ifndef FLAME_H
+#define FLAME_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FLAME_OK = 0,
+    FLAME_ERR_PARAM = 1,     /* invalid argument or parameter                          */
+    FLAME_ERR_CFL = 2,       /* whistler CFL violated and strict_cfl set (flame_init)   */
+    FLAME_ERR_NONFINITE = 3, /* a non-finite density, velocity or field was produced   */
+    FLAME_ERR_CUDA = 4,      /* a CUDA runtime or cuFFT call failed                     */
+    FLAME_ERR_STATE = 5      /* state blob or call order inconsistent                   */
+} flame_status;
+
+typedef enum { FLAME_FP32 = 1, FLAME_FP16 = 2, FLAME_BF16 = 3 } flame_storage;
+
+typedef struct {
+    int nx, ny, nz;   /* lattice size, each >= 1                                          */
+    double tau_nu;    /* fluid relaxation time 1/omega = nu/c_s^2 + 1/2 > 1/2 (Sec. 3.1.1) */
+    double tau_eta;   /* magnetic relaxation time 1/omega_B = eta/C^2 + 1/2 > 1/2 (Sec. 3.2) */
+    double d_i;       /* Hall coefficient alpha_H, the ion inertial length in lattice
+                         units (Sec. 3.3 with U_0 = V_A, rho = 1); 0 gives resistive MHD   */
+    int storage;      /* flame_storage                                                    */
+    double rho0;      /* reference density of the deviation encoding (> 0, normally 1)   */
+    double B_ref[3];  /* reference field of the deviation encoding (normally the mean
+                         field, which the scheme conserves exactly)                       */
+    int init_noneq;   /* 1: flame_init adds the first-order non-equilibrium parts        */
+    int check_every;  /* > 0: flame_step synchronises and checks the non-finite flag
+                         every check_every steps; 0: only flame_sync checks               */
+    int strict_cfl;   /* 1: flame_init fails with FLAME_ERR_CFL if pi d_i max(V_A,|u|) > 1 */
+} flame_params;
+
+typedef struct {
+    long long step;   /* steps taken since flame_init / flame_set_state             */
+    int parity;       /* AA parity: 0 = every slot holds its natural population     */
+    int nonfinite;    /* sticky non-finite flag (read at the last synchronising call) */
+    double cfl;       /* pi d_i max(V_A, |u|) of the initial fields (Sec. 3.4)       */
+    double max_speed; /* max over sites of max(|B|/sqrt(rho), |u|) at flame_init      */
+} flame_info_t;
+
+/* Scalar diagnostics written by flame_reduce (indices into h_scalars). */
+enum {
+    FLAME_S_MASS = 0,       /* sum rho                                          */
+    FLAME_S_MOMX = 1,       /* sum rho u_x (2: y, 3: z)                         */
+    FLAME_S_BX = 4,         /* <B_x> (5: y, 6: z)                               */
+    FLAME_S_EU = 7,         /* 1/2 <|u|^2>                                      */
+    FLAME_S_EB = 8,         /* 1/2 <|B - <B>|^2>                                */
+    FLAME_S_HC = 9,         /* <u . (B - <B>)>, cross-helicity                   */
+    FLAME_S_J2 = 10,        /* <|J|^2>; eta <|J|^2> is the magnetic dissipation  */
+    FLAME_S_UMAX = 11,      /* max |u|                                          */
+    FLAME_S_DIVB = 12,      /* rms of -(omega_B/C^2) Tr(Lambda), eq. LB_B_div     */
+    FLAME_S_NONFINITE = 13, /* number of sites with a non-finite moment         */
+    FLAME_NSCALARS = 14
+};
+
+typedef struct flame_ctx flame_ctx;
+
+/* Bytes of the population state: 48 * N3 * (4 for FP32, 2 for FP16/BF16).
+ * Returns 0 for invalid parameters. */
+size_t flame_state_bytes(const flame_params *p);
+
+/* Create a context over caller-owned device state d_state (flame_state_bytes,
+ * 256-byte aligned) and a cudaStream_t `stream` (NULL: legacy default
+ * stream).  Checks: sizes >= 1, ny and nz <= 65535, N3 < 2^31, tau > 1/2, rho0 > 0, finite
+ * d_i >= 0, valid storage.  Errors: FLAME_ERR_PARAM (then *out = NULL),
+ * FLAME_ERR_CUDA if the current device cannot be queried. */
+flame_status flame_create(flame_ctx **out, const flame_params *p, void *d_state, void *stream);
+
+/* Fill the state with the populations of the initial fields (time t = 0):
+ * f = f^mhd(0)(rho, u, B) (Sec. 3.1.1: 6th-order Hermite equilibrium plus
+ * the Lorentz stress term) and g = g^Hall(0)(u, B, J0) (eq. gHall_eq) with
+ * J0 = curl B; with init_noneq, plus the first-order non-equilibrium parts
+ * -(rho c_s^2/omega)(grad u + grad u^T) projected on w_i H2_i/(2 c_s^4) for
+ * f and -(W_i/omega_B) xi_ia d_a B_b for g, which make the step's current
+ * equal curl B at t = 0.  d_rho [N3] may be NULL (rho = 1); d_u, d_B [3][N3]
+ * are required; d_gradu, d_gradB [9][N3] may be NULL (periodic second-order
+ * central differences of d_u, d_B).  All FP64.  Resets step and parity.
+ * Synchronises to evaluate the whistler CFL number pi d_i max(V_A, |u|)
+ * (Sec. 3.4): FLAME_ERR_CFL if it exceeds 1 and strict_cfl is set. */
+flame_status flame_init(flame_ctx *ctx, const double *d_rho, const double *d_u, const double *d_B,
+                        const double *d_gradu, const double *d_gradB);
+
+/* Advance n >= 0 time steps, one fused kernel launch per step: moments
+ * (eqs. LB_moments2, mag_field_LB), current from the 3x3 Hall system (eqs.
+ * LB_density_current, soe_current_density), central-moment fluid collision
+ * (eqs. cm_collision_step, collision_matrix), Hall-equilibrium BGK magnetic
+ * collision (eqs. gHall_eq, MHD_LBscheme) and periodic streaming (eq. stream),
+ * in place.  Asynchronous unless check_every > 0.  Errors: FLAME_ERR_PARAM
+ * (n < 0), FLAME_ERR_STATE (flame_init not called), sticky errors. */
+flame_status flame_step(flame_ctx *ctx, int n);
+
+/* Synchronise the stream and report sticky errors (CUDA, non-finite). */
+flame_status flame_sync(flame_ctx *ctx);
+
+/* Step count, parity, CFL number and the sticky non-finite flag. */
+flame_status flame_info(flame_ctx *ctx, flame_info_t *out);
+
+/* Macroscopic fields of the current pre-collision populations, FP64:
+ * rho [N3], u [3][N3], B [3][N3], J [3][N3] (J from the Hall linear system,
+ * as in the step).  Any pointer may be NULL.  Asynchronous. */
+flame_status flame_moments(flame_ctx *ctx, double *d_rho, double *d_u, double *d_B, double *d_J);
+
+/* The current pre-collision populations decoded to FP64 in natural order,
+ * d_f [48][N3] with the slot numbering above, whatever the AA parity.
+ * Asynchronous. */
+flame_status flame_populations(flame_ctx *ctx, double *d_f);
+
+/* FP64 scalar diagnostics of the current state (Sec. 4.3, 5: energies,
+ * cross-helicity, magnetic dissipation, div B estimate).  h_scalars has
+ * FLAME_NSCALARS entries (indices FLAME_S_*).  Synchronises. */
+flame_status flame_reduce(flame_ctx *ctx, double *h_scalars);
+
+/* Shell energy spectra of u and B - <B> (Sec. 4.3): with
+ * F_hat(m) = N3^-1 sum_x F(x) exp(-2 pi i m.x/N), h_Eu[n] and h_Eb[n] are
+ * 1/2 sum |F_hat|^2 over the modes with round(|m|) = n, n = 0..nshell-1
+ * (modes beyond are dropped; summed over every shell they give 1/2<|F|^2>);
+ * 1 <= nshell <= 4096, else FLAME_ERR_PARAM.
+ * FFTs by cuFFT (FP64), shell sums in FP64.  Either output may be NULL.
+ * Synchronises. */
+flame_status flame_spectra(flame_ctx *ctx, int nshell, double *h_Eu, double *h_Eb);
+
+/* Copy the raw population state (flame_state_bytes) to d_dst, with the step
+ * count and parity needed to resume.  Asynchronous. */
+flame_status flame_get_state(flame_ctx *ctx, void *d_dst, long long *step, int *parity);
+
+/* Replace the population state with d_src (flame_state_bytes, written by
+ * flame_get_state with the same parameters) and set step and parity.
+ * Errors: FLAME_ERR_STATE (parity not 0/1, step < 0).  Asynchronous. */
+flame_status flame_set_state(flame_ctx *ctx, const void *d_src, long long step, int parity);
+
+/* Release the context and its internal workspace (not the caller's state). */
+void flame_destroy(flame_ctx *ctx);
+
+/* Human-readable text of a status code (static storage). */
+const char *flame_status_string(flame_status s);
+
+/* The velocity tables the kernels use: c27 [27*3] (App. A order) and
+ * xi7 [7*3].  Returns 0. Host only, no GPU needed. */
+int flame_lattice(int *c27, int *xi7);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,17 @@
+"""GB300-native fused lattice-Boltzmann time step for 3-D periodic Hall-MHD.
+
+The method is the FLAME scheme of Foldes et al. (arXiv 2212.11024): a D3Q27
+central-moment fluid (Sec. 3.1) coupled to three D3Q7 BGK magnetic
+populations whose equilibrium carries the Hall term (Sec. 3.2), with the
+current obtained from the magnetic non-equilibrium moments.
+
+- ``Flame``   : ctypes binding of libflame.so (include/flame.h); CUDA only.
+- ``inputs``  : seeded synthetic initial conditions (numpy).
+- ``units``   : lattice-unit parameter mapping and the whistler CFL check.
+- ``build``   : nvcc build of libflame.so for sm_103a.
+"""
+from . import inputs, units
+from .flame import Flame, FlameError, FlameUnavailable, lattice, library, make_params, state_bytes
+
+__all__ = ["Flame", "FlameError", "FlameUnavailable", "inputs", "units", "lattice", "library", "make_params",
+           "state_bytes"]

@@ -1,0 +1,443 @@
+// api.cu -- the C ABI declared in include/flame.h.
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/flame.h"
+#include "flame_internal.h"
+#include "lattice.cuh"
+
+struct flame_ctx {
+  flame_params p;
+  void* state;
+  cudaStream_t stream;
+  int device;
+  int nsm;
+  long long step;
+  int parity;
+  bool initialized;
+  flame_status sticky;
+  double cfl, max_speed;
+  int nonfinite;
+  unsigned* d_flags;  // [0] non-finite flag, [1] max speed (float bits)
+  // internal workspace (lazily allocated)
+  double* d_red;      // kRedBlocksMax * kRedVals partials + kRedVals result
+  double* d_fields;   // 6 * N3 doubles (u, B) for spectra
+  void* d_spec;       // nz * ny * (nx/2+1) cufftDoubleComplex
+  double* d_shells;   // 2 * nshell_cap doubles
+  int nshell_cap;
+  cufftHandle plan;
+  bool has_plan;
+  flame::StepConsts k;
+  flame::Grid g;
+};
+
+namespace {
+
+size_t elem_bytes(int storage) { return storage == FLAME_FP32 ? 4 : (storage == FLAME_FP16 || storage == FLAME_BF16) ? 2 : 0; }
+
+flame_status check_params(const flame_params* p) {
+  if (!p) return FLAME_ERR_PARAM;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return FLAME_ERR_PARAM;
+  if (p->ny > 65535 || p->nz > 65535) return FLAME_ERR_PARAM;  // grid y / z launch dimensions
+  const long long n3 = (long long)p->nx * p->ny * p->nz;
+  if (n3 >= (1ll << 31)) return FLAME_ERR_PARAM;
+  if (!(p->tau_nu > 0.5) || !(p->tau_eta > 0.5) || !std::isfinite(p->tau_nu) || !std::isfinite(p->tau_eta))
+    return FLAME_ERR_PARAM;
+  if (!(p->d_i >= 0.0) || !std::isfinite(p->d_i)) return FLAME_ERR_PARAM;
+  if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return FLAME_ERR_PARAM;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p->B_ref[a])) return FLAME_ERR_PARAM;
+  if (elem_bytes(p->storage) == 0) return FLAME_ERR_PARAM;
+  if (p->check_every < 0) return FLAME_ERR_PARAM;
+  return FLAME_OK;
+}
+
+flame_status cuda_fail(flame_ctx* c, cudaError_t e) {
+  if (e == cudaSuccess) return FLAME_OK;
+  if (c && c->sticky == FLAME_OK) c->sticky = FLAME_ERR_CUDA;
+  return FLAME_ERR_CUDA;
+}
+
+flame_status usable(flame_ctx* c) {
+  if (!c) return FLAME_ERR_PARAM;
+  if (c->sticky != FLAME_OK) return c->sticky;
+  return FLAME_OK;
+}
+
+// Synchronise, then fold CUDA errors and the non-finite flag into the
+// sticky status.
+flame_status sync_and_check(flame_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  unsigned flag = 0;
+  e = cudaMemcpy(&flag, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  if (flag) {
+    c->nonfinite = 1;
+    if (c->sticky == FLAME_OK) c->sticky = FLAME_ERR_NONFINITE;
+  }
+  return c->sticky;
+}
+
+int reduce_blocks(const flame_ctx* c) {
+  long long want = (long long)c->nsm * 4;
+  const long long per = (c->g.n3 + 255) / 256;
+  if (want > per) want = per;
+  if (want < 1) want = 1;
+  if (want > flame::kRedBlocksMax) want = flame::kRedBlocksMax;
+  return (int)want;
+}
+
+// FP64 power of a D2Z half spectrum binned into integer shells.
+__global__ void shell_bin_kernel(const cufftDoubleComplex* __restrict__ F, flame::Grid g, int nshell,
+                                 int zero_mean, double* __restrict__ shells) {
+  extern __shared__ double hist[];
+  for (int i = threadIdx.x; i < nshell; i += blockDim.x) hist[i] = 0.0;
+  __syncthreads();
+  const int hx = g.nx / 2 + 1;
+  const long long total = (long long)g.nz * g.ny * hx;
+  const double inv = 1.0 / ((double)g.n3 * (double)g.n3);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(t % hx);
+    const int ky = (int)((t / hx) % g.ny);
+    const int kz = (int)(t / ((long long)hx * g.ny));
+    const int my = ky <= g.ny / 2 ? ky : ky - g.ny;
+    const int mz = kz <= g.nz / 2 ? kz : kz - g.nz;
+    if (zero_mean && kx == 0 && my == 0 && mz == 0) continue;
+    const long long m2 = (long long)kx * kx + (long long)my * my + (long long)mz * mz;
+    const int n = __double2int_rn(sqrt((double)m2));
+    if (n >= nshell) continue;
+    const double w = (kx == 0 || (g.nx % 2 == 0 && kx == g.nx / 2)) ? 1.0 : 2.0;
+    const cufftDoubleComplex v = F[t];
+    atomicAdd(&hist[n], w * (v.x * v.x + v.y * v.y) * inv);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nshell; i += blockDim.x)
+    if (hist[i] != 0.0) atomicAdd(&shells[i], hist[i]);
+}
+
+}  // namespace
+
+namespace flame {
+cudaError_t launch_shell_bin(const void* spec, Grid g, int nshell, int zero_mean, double* shells, cudaStream_t s) {
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  shell_bin_kernel<<<nsm * 2, 256, (size_t)nshell * sizeof(double), s>>>(
+      static_cast<const cufftDoubleComplex*>(spec), g, nshell, zero_mean, shells);
+  return cudaGetLastError();
+}
+}  // namespace flame
+
+extern "C" {
+
+size_t flame_state_bytes(const flame_params* p) {
+  if (check_params(p) != FLAME_OK) return 0;
+  return (size_t)flame::kPop * (size_t)p->nx * (size_t)p->ny * (size_t)p->nz * elem_bytes(p->storage);
+}
+
+flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state, void* stream) {
+  if (!out) return FLAME_ERR_PARAM;
+  *out = nullptr;
+  flame_status st = check_params(p);
+  if (st != FLAME_OK) return st;
+  if (!d_state || (reinterpret_cast<uintptr_t>(d_state) & 255u) != 0) return FLAME_ERR_PARAM;
+  flame_ctx* c = new (std::nothrow) flame_ctx;
+  if (!c) return FLAME_ERR_PARAM;
+  std::memset(static_cast<void*>(c), 0, sizeof(*c));
+  c->p = *p;
+  c->state = d_state;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->sticky = FLAME_OK;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return FLAME_ERR_CUDA;
+  }
+  if (cudaMalloc(&c->d_flags, 2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(unsigned), c->stream) != cudaSuccess) {
+    cudaFree(c->d_flags);
+    delete c;
+    return FLAME_ERR_CUDA;
+  }
+  c->k.omega = (float)(1.0 / p->tau_nu);
+  c->k.omegaB = (float)(1.0 / p->tau_eta);
+  c->k.alphaH = (float)p->d_i;
+  c->k.rho0 = (float)p->rho0;
+  for (int a = 0; a < 3; ++a) c->k.Bref[a] = (float)p->B_ref[a];
+  c->g.nx = p->nx;
+  c->g.ny = p->ny;
+  c->g.nz = p->nz;
+  c->g.n3 = (long long)p->nx * p->ny * p->nz;
+  *out = c;
+  return FLAME_OK;
+}
+
+flame_status flame_init(flame_ctx* c, const double* d_rho, const double* d_u, const double* d_B,
+                        const double* d_gradu, const double* d_gradB) {
+  if (!c) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  if (!d_u || !d_B) return FLAME_ERR_PARAM;
+  // a fresh initial state clears a previous non-finite condition
+  c->sticky = FLAME_OK;
+  c->nonfinite = 0;
+  cudaError_t e = cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  e = flame::launch_init(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu, d_gradB,
+                         c->d_flags + 1, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  unsigned bits = 0;
+  e = cudaMemcpyAsync(&bits, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  float sp;
+  std::memcpy(&sp, &bits, sizeof(sp));
+  c->max_speed = sp;
+  c->cfl = M_PI * c->p.d_i * c->max_speed;
+  c->step = 0;
+  c->parity = 0;
+  c->initialized = true;
+  if (!std::isfinite(c->max_speed)) {
+    c->nonfinite = 1;
+    c->sticky = FLAME_ERR_NONFINITE;
+    return c->sticky;
+  }
+  if (c->p.strict_cfl && c->cfl > 1.0) return FLAME_ERR_CFL;
+  return FLAME_OK;
+}
+
+flame_status flame_step(flame_ctx* c, int n) {
+  flame_status st = usable(c);
+  if (st != FLAME_OK) return st;
+  if (n < 0) return FLAME_ERR_PARAM;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  for (int i = 0; i < n; ++i) {
+    cudaError_t e = flame::launch_step(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->parity ^= 1;
+    ++c->step;
+    if (c->p.check_every > 0 && c->step % c->p.check_every == 0) {
+      st = sync_and_check(c);
+      if (st != FLAME_OK) return st;
+    }
+  }
+  return FLAME_OK;
+}
+
+flame_status flame_sync(flame_ctx* c) {
+  if (!c) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  return sync_and_check(c);
+}
+
+flame_status flame_info(flame_ctx* c, flame_info_t* out) {
+  if (!c || !out) return FLAME_ERR_PARAM;
+  out->step = c->step;
+  out->parity = c->parity;
+  out->nonfinite = c->nonfinite;
+  out->cfl = c->cfl;
+  out->max_speed = c->max_speed;
+  return FLAME_OK;
+}
+
+flame_status flame_moments(flame_ctx* c, double* d_rho, double* d_u, double* d_B, double* d_J) {
+  flame_status st = usable(c);
+  if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  return cuda_fail(c, flame::launch_moments(c->p.storage, c->parity, c->state, c->g, c->k, d_rho, d_u, d_B, d_J,
+                                            c->stream));
+}
+
+flame_status flame_populations(flame_ctx* c, double* d_f) {
+  flame_status st = usable(c);
+  if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  if (!d_f) return FLAME_ERR_PARAM;
+  return cuda_fail(c, flame::launch_populations(c->p.storage, c->parity, c->state, c->g, c->k, d_f, c->stream));
+}
+
+flame_status flame_reduce(flame_ctx* c, double* h) {
+  flame_status st = usable(c);
+  if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  if (!h) return FLAME_ERR_PARAM;
+  cudaError_t e;
+  if (!c->d_red) {
+    e = cudaMalloc(&c->d_red, sizeof(double) * (size_t)(flame::kRedBlocksMax + 1) * flame::kRedVals);
+    if (e != cudaSuccess) {
+      c->d_red = nullptr;
+      return cuda_fail(c, e);
+    }
+  }
+  const int nb = reduce_blocks(c);
+  double* out = c->d_red + (size_t)flame::kRedBlocksMax * flame::kRedVals;
+  e = flame::launch_reduce(c->p.storage, c->parity, c->state, c->g, c->k, nb, c->d_red, out, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  double r[flame::kRedVals];
+  e = cudaMemcpyAsync(r, out, sizeof(r), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  const double n3 = (double)c->g.n3;
+  double Bm[3];
+  h[FLAME_S_MASS] = r[0];
+  for (int a = 0; a < 3; ++a) {
+    h[FLAME_S_MOMX + a] = r[1 + a];
+    Bm[a] = r[4 + a] / n3;
+    h[FLAME_S_BX + a] = Bm[a];
+  }
+  h[FLAME_S_EU] = 0.5 * r[7] / n3;
+  double dbm2 = 0.0, hc_corr = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double d = Bm[a] - c->p.B_ref[a];
+    dbm2 += d * d;
+    hc_corr += (r[10 + a] / n3) * d;
+  }
+  h[FLAME_S_EB] = 0.5 * (r[8] / n3 - dbm2);
+  h[FLAME_S_HC] = r[9] / n3 - hc_corr;
+  h[FLAME_S_J2] = r[13] / n3;
+  h[FLAME_S_UMAX] = r[14];
+  h[FLAME_S_DIVB] = std::sqrt(r[15] / n3);
+  h[FLAME_S_NONFINITE] = r[16];
+  return r[16] > 0 ? FLAME_ERR_NONFINITE : FLAME_OK;
+}
+
+flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb) {
+  flame_status st = usable(c);
+  if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  if (nshell < 1 || nshell > 4096) return FLAME_ERR_PARAM;  // shell histogram lives in shared memory
+  cudaError_t e;
+  const size_t n3 = (size_t)c->g.n3;
+  const size_t nc = (size_t)c->g.nz * c->g.ny * (c->g.nx / 2 + 1);
+  if (!c->d_fields) {
+    e = cudaMalloc(&c->d_fields, 6 * n3 * sizeof(double));
+    if (e != cudaSuccess) {
+      c->d_fields = nullptr;
+      return cuda_fail(c, e);
+    }
+  }
+  if (!c->d_spec) {
+    e = cudaMalloc(&c->d_spec, nc * sizeof(cufftDoubleComplex));
+    if (e != cudaSuccess) {
+      c->d_spec = nullptr;
+      return cuda_fail(c, e);
+    }
+  }
+  if (nshell > c->nshell_cap) {
+    cudaFree(c->d_shells);
+    c->d_shells = nullptr;
+    e = cudaMalloc(&c->d_shells, 2 * (size_t)nshell * sizeof(double));
+    if (e != cudaSuccess) {
+      c->nshell_cap = 0;
+      return cuda_fail(c, e);
+    }
+    c->nshell_cap = nshell;
+  }
+  if (!c->has_plan) {
+    if (cufftPlan3d(&c->plan, c->g.nz, c->g.ny, c->g.nx, CUFFT_D2Z) != CUFFT_SUCCESS) return cuda_fail(c, cudaErrorUnknown);
+    c->has_plan = true;
+  }
+  if (cufftSetStream(c->plan, c->stream) != CUFFT_SUCCESS) return cuda_fail(c, cudaErrorUnknown);
+  double* u = c->d_fields;
+  double* B = c->d_fields + 3 * n3;
+  e = flame::launch_moments(c->p.storage, c->parity, c->state, c->g, c->k, nullptr, u, B, nullptr, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_shells, 0, 2 * (size_t)nshell * sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  for (int f = 0; f < 6; ++f) {
+    double* src = c->d_fields + (size_t)f * n3;
+    if (cufftExecD2Z(c->plan, src, static_cast<cufftDoubleComplex*>(c->d_spec)) != CUFFT_SUCCESS)
+      return cuda_fail(c, cudaErrorUnknown);
+    e = flame::launch_shell_bin(c->d_spec, c->g, nshell, f >= 3, c->d_shells + (f >= 3 ? nshell : 0), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+  }
+  double* tmp = static_cast<double*>(std::malloc(2 * (size_t)nshell * sizeof(double)));
+  if (!tmp) return FLAME_ERR_PARAM;
+  e = cudaMemcpyAsync(tmp, c->d_shells, 2 * (size_t)nshell * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    std::free(tmp);
+    return cuda_fail(c, e);
+  }
+  for (int i = 0; i < nshell; ++i) {
+    if (h_Eu) h_Eu[i] = 0.5 * tmp[i];
+    if (h_Eb) h_Eb[i] = 0.5 * tmp[nshell + i];
+  }
+  std::free(tmp);
+  return FLAME_OK;
+}
+
+flame_status flame_get_state(flame_ctx* c, void* d_dst, long long* step, int* parity) {
+  if (!c || !d_dst) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  cudaError_t e = cudaMemcpyAsync(d_dst, c->state, flame_state_bytes(&c->p), cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  if (step) *step = c->step;
+  if (parity) *parity = c->parity;
+  return FLAME_OK;
+}
+
+flame_status flame_set_state(flame_ctx* c, const void* d_src, long long step, int parity) {
+  if (!c || !d_src) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  if ((parity != 0 && parity != 1) || step < 0) return FLAME_ERR_STATE;
+  cudaError_t e = cudaMemcpyAsync(c->state, d_src, flame_state_bytes(&c->p), cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  e = cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->sticky = FLAME_OK;
+  c->nonfinite = 0;
+  c->step = step;
+  c->parity = parity;
+  c->initialized = true;
+  return FLAME_OK;
+}
+
+void flame_destroy(flame_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->has_plan) cufftDestroy(c->plan);
+  cudaFree(c->d_flags);
+  cudaFree(c->d_red);
+  cudaFree(c->d_fields);
+  cudaFree(c->d_spec);
+  cudaFree(c->d_shells);
+  delete c;
+}
+
+const char* flame_status_string(flame_status s) {
+  switch (s) {
+    case FLAME_OK: return "ok";
+    case FLAME_ERR_PARAM: return "invalid parameter";
+    case FLAME_ERR_CFL: return "whistler CFL condition violated";
+    case FLAME_ERR_NONFINITE: return "non-finite value in the state";
+    case FLAME_ERR_CUDA: return "CUDA error";
+    case FLAME_ERR_STATE: return "inconsistent state or call order";
+  }
+  return "unknown status";
+}
+
+int flame_lattice(int* c27, int* xi7) {
+  for (int i = 0; i < flame::kQ; ++i) {
+    if (c27) {
+      c27[3 * i + 0] = flame::cx27(i);
+      c27[3 * i + 1] = flame::cy27(i);
+      c27[3 * i + 2] = flame::cz27(i);
+    }
+  }
+  for (int i = 0; i < flame::kM; ++i) {
+    if (xi7) {
+      xi7[3 * i + 0] = flame::mx7(i);
+      xi7[3 * i + 1] = flame::my7(i);
+      xi7[3 * i + 2] = flame::mz7(i);
+    }
+  }
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// flame_internal.h -- kernel launchers shared by the translation units of
+// libflame.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace flame {
+
+// Per-run constants of the step (lattice units).
+struct StepConsts {
+  float omega;    // 1 / tau_nu          (Sec. 3.1.1)
+  float omegaB;   // 1 / tau_eta         (Sec. 3.2)
+  float alphaH;   // Hall coefficient d_i
+  float rho0;     // reference density of the deviation encoding
+  float Bref[3];  // reference field of the deviation encoding
+};
+
+struct Grid {
+  int nx, ny, nz;
+  long long n3;
+};
+
+// storage: 1 FP32, 2 FP16, 3 BF16 (flame_storage)
+cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
+                        cudaStream_t s);
+
+cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
+                        const double* u, const double* B, const double* gu, const double* gB,
+                        unsigned* speed_bits, cudaStream_t s);
+
+cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* rho,
+                           double* u, double* B, double* J, cudaStream_t s);
+
+cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, const StepConsts& k,
+                               double* f, cudaStream_t s);
+
+// Number of FP64 partial sums per block written by the reduction.
+constexpr int kRedVals = 17;
+// Upper bound on the reduction's block count (its partials fill
+// kRedBlocksMax * kRedVals doubles of scratch).
+constexpr int kRedBlocksMax = 1024;
+
+cudaError_t launch_reduce(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
+                          double* partials, double* out, cudaStream_t s);
+
+cudaError_t launch_shell_bin(const void* spec /* cufftDoubleComplex */, Grid g, int nshell, int zero_mean,
+                             double* shells, cudaStream_t s);
+
+}  // namespace flame

@@ -1,0 +1,80 @@
+// lattice.cuh -- lattice constants and storage encodings of the GB300 FLAME
+// step.  Lattice units throughout: dx = dt = 1, c_s^2 = 1/3 (Sec. 3.1.1),
+// C^2 = 1/4 from 2C = sqrt(3) c_s (eq. lattice_coincidence).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace flame {
+
+constexpr int kQ = 27;    // D3Q27 fluid velocities
+constexpr int kM = 7;     // D3Q7 magnetic velocities
+constexpr int kPop = 48;  // 27 + 3 * 7 populations per site
+
+// App. A velocity set, in the paper's order (i and i+13 are opposite).
+__host__ __device__ constexpr int cx27(int i) {
+  constexpr int t[kQ] = {0, -1, 0, 0, -1, -1, -1, -1, 0, 0, -1, -1, -1, -1, 1, 0, 0, 1, 1, 1, 1, 0, 0, 1, 1, 1, 1};
+  return t[i];
+}
+__host__ __device__ constexpr int cy27(int i) {
+  constexpr int t[kQ] = {0, 0, -1, 0, -1, 1, 0, 0, -1, -1, -1, -1, 1, 1, 0, 1, 0, 1, -1, 0, 0, 1, 1, 1, 1, -1, -1};
+  return t[i];
+}
+__host__ __device__ constexpr int cz27(int i) {
+  constexpr int t[kQ] = {0, 0, 0, -1, 0, 0, -1, 1, -1, 1, -1, 1, -1, 1, 0, 0, 1, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+  return t[i];
+}
+
+// D3Q7 (Sec. 3.2): rest, +x, -x, +y, -y, +z, -z.
+__host__ __device__ constexpr int mx7(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+__host__ __device__ constexpr int my7(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
+__host__ __device__ constexpr int mz7(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
+
+__host__ __device__ constexpr int opp27(int i) { return i == 0 ? 0 : (i <= 13 ? i + 13 : i - 13); }
+__host__ __device__ constexpr int opp7(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Slot of a population in the 48-slot state: fluid q, magnetic 27 + 7b + i.
+__host__ __device__ constexpr int mslot(int b, int i) { return kQ + kM * b + i; }
+
+// Sec. 3.1.1 weights by |c|^2 (8/27, 2/27, 1/54, 1/216); they factor into
+// the 1-D weights 2/3 (c = 0) and 1/6 (c = +-1).
+__host__ __device__ constexpr double w27d(int i) {
+  return (cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i)) == 0   ? 8.0 / 27.0
+         : (cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i)) == 1 ? 2.0 / 27.0
+         : (cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i)) == 2 ? 1.0 / 54.0
+                                                                            : 1.0 / 216.0;
+}
+// Sec. 3.2 weights: 1/4 rest, 1/8 faces.
+__host__ __device__ constexpr double w7d(int i) { return i == 0 ? 0.25 : 0.125; }
+
+// ---------------------------------------------------------------------------
+// Storage encodings.  A slot holds s = (population - reference) / weight in
+// one of three element types; decode gives FP32, encode rounds to nearest
+// even.
+template <class T>
+struct Codec;
+
+template <>
+struct Codec<float> {
+  static __device__ __forceinline__ float load(const float* p) { return *p; }
+  static __device__ __forceinline__ float dec(float v) { return v; }
+  static __device__ __forceinline__ float enc(float v) { return v; }
+};
+
+template <>
+struct Codec<__half> {
+  static __device__ __forceinline__ __half load(const __half* p) { return *p; }
+  static __device__ __forceinline__ float dec(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half enc(float v) { return __float2half_rn(v); }
+};
+
+template <>
+struct Codec<__nv_bfloat16> {
+  static __device__ __forceinline__ __nv_bfloat16 load(const __nv_bfloat16* p) { return *p; }
+  static __device__ __forceinline__ float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v) { return __float2bfloat16_rn(v); }
+};
+
+}  // namespace flame

@@ -1,0 +1,261 @@
+"""Python binding of libflame.so (include/flame.h): argument marshalling only.
+
+PyTorch supplies device memory and streams; every step of the method runs
+in the library's CUDA kernels.  There is no CPU fallback: without the
+compiled library, or without a CUDA device, the constructors raise.
+
+    from paper_2212_11024_gb300 import Flame, inputs
+    u, B = inputs.turbulence((128, 128, 128), 1, 2)
+    sim = Flame(128, 128, 128, tau_nu=0.51, tau_eta=0.51, d_i=6.4, storage="fp16")
+    sim.init(None, u, B)
+    sim.step(100)
+    m = sim.moments()          # dict of FP64 CUDA tensors rho, u, B, J
+    Eu, Eb = sim.spectra(65)   # shell spectra, numpy FP64
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libflame.so")
+
+FLAME_OK, FLAME_ERR_PARAM, FLAME_ERR_CFL, FLAME_ERR_NONFINITE, FLAME_ERR_CUDA, FLAME_ERR_STATE = range(6)
+STORAGE = {"fp32": 1, "fp16": 2, "bf16": 3}
+NSCALARS = 14
+SCALAR_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "B_x", "B_y", "B_z", "E_u", "E_B", "H_c", "J2", "u_max",
+                "divB_rms", "nonfinite"]
+
+
+class FlameError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib().flame_status_string(status).decode()} (status {status})")
+
+
+class FlameUnavailable(RuntimeError):
+    pass
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("tau_nu", ctypes.c_double), ("tau_eta", ctypes.c_double), ("d_i", ctypes.c_double),
+        ("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("B_ref", ctypes.c_double * 3),
+        ("init_noneq", ctypes.c_int), ("check_every", ctypes.c_int), ("strict_cfl", ctypes.c_int),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("parity", ctypes.c_int), ("nonfinite", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("max_speed", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    with _lock:
+        if _LIB is not None:
+            return _LIB
+        if not os.path.exists(LIB_PATH):
+            raise FlameUnavailable(f"{LIB_PATH} is missing: build it with paper_2212_11024_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, P, i, d = ctypes.c_void_p, ctypes.POINTER, ctypes.c_int, ctypes.c_double
+        sig = {
+            "flame_state_bytes": (ctypes.c_size_t, [P(Params)]),
+            "flame_create": (i, [P(vp), P(Params), vp, vp]),
+            "flame_init": (i, [vp, vp, vp, vp, vp, vp]),
+            "flame_step": (i, [vp, i]),
+            "flame_sync": (i, [vp]),
+            "flame_info": (i, [vp, P(Info)]),
+            "flame_moments": (i, [vp, vp, vp, vp, vp]),
+            "flame_populations": (i, [vp, vp]),
+            "flame_reduce": (i, [vp, P(d)]),
+            "flame_spectra": (i, [vp, i, P(d), P(d)]),
+            "flame_get_state": (i, [vp, vp, P(ctypes.c_longlong), P(i)]),
+            "flame_set_state": (i, [vp, vp, ctypes.c_longlong, i]),
+            "flame_destroy": (None, [vp]),
+            "flame_status_string": (ctypes.c_char_p, [i]),
+            "flame_lattice": (i, [P(i), P(i)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+        return lib
+
+
+def library():
+    """The loaded ctypes library (raises FlameUnavailable if not built)."""
+    return _lib()
+
+
+def lattice():
+    """(c27 [27,3], xi7 [7,3]) velocity tables compiled into the kernels."""
+    c = (ctypes.c_int * 81)()
+    x = (ctypes.c_int * 21)()
+    _lib().flame_lattice(c, x)
+    return np.array(c[:]).reshape(27, 3), np.array(x[:]).reshape(7, 3)
+
+
+def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
+                init_noneq=True, check_every=0, strict_cfl=False) -> Params:
+    p = Params()
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    p.tau_nu, p.tau_eta, p.d_i = float(tau_nu), float(tau_eta), float(d_i)
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.rho0 = float(rho0)
+    for a in range(3):
+        p.B_ref[a] = float(B_ref[a])
+    p.init_noneq, p.check_every, p.strict_cfl = int(bool(init_noneq)), int(check_every), int(bool(strict_cfl))
+    return p
+
+
+def state_bytes(p: Params) -> int:
+    return int(_lib().flame_state_bytes(ctypes.byref(p)))
+
+
+def _check(rc, what):
+    if rc != FLAME_OK:
+        raise FlameError(rc, what)
+
+
+class Flame:
+    """One periodic Hall-MHD lattice on one GPU (a flame_ctx plus its state)."""
+
+    def __init__(self, nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
+                 init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise FlameUnavailable("no CUDA device: the FLAME step runs only on the GPU")
+        lib = _lib()
+        self.torch = torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.p = make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage, rho0, B_ref, init_noneq, check_every,
+                             strict_cfl)
+        self.shape = (int(nz), int(ny), int(nx))
+        self.n3 = int(nx) * int(ny) * int(nz)
+        nbytes = state_bytes(self.p)
+        if nbytes == 0:
+            raise FlameError(FLAME_ERR_PARAM, "flame_state_bytes")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.state = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            ctx = ctypes.c_void_p()
+            _check(lib.flame_create(ctypes.byref(ctx), ctypes.byref(self.p), ctypes.c_void_p(self.state.data_ptr()),
+                                    ctypes.c_void_p(self.stream.cuda_stream)), "flame_create")
+        self._ctx = ctx
+        self._lib = lib
+
+    # ------------------------------------------------------------------ util
+    def _dev(self, a, ncomp):
+        """FP64 contiguous device tensor of shape [ncomp, nz, ny, nx] (or [nz,ny,nx])."""
+        if a is None:
+            return None
+        t = self.torch
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+        a = a.to(device=self.device, dtype=t.float64).contiguous()
+        want = (ncomp,) + self.shape if ncomp else self.shape
+        if tuple(a.shape) != want:
+            raise ValueError(f"expected shape {want}, got {tuple(a.shape)}")
+        return a
+
+    @staticmethod
+    def _ptr(a):
+        return ctypes.c_void_p(a.data_ptr()) if a is not None else None
+
+    def _ctx_or_raise(self):
+        if self._ctx is None:
+            raise RuntimeError("context closed")
+        return self._ctx
+
+    # ------------------------------------------------------------------- API
+    def init(self, rho, u, B, gradu=None, gradB=None):
+        """flame_init from FP64 fields (numpy or torch): rho [nz,ny,nx] or None,
+        u, B [3,nz,ny,nx], optional gradients [9,nz,ny,nx]."""
+        r, uu, bb = self._dev(rho, 0), self._dev(u, 3), self._dev(B, 3)
+        gu, gb = self._dev(gradu, 9), self._dev(gradB, 9)
+        with self.torch.cuda.device(self.device), self.torch.cuda.stream(self.stream):
+            # flame_init synchronises the stream, so the temporaries outlive their use
+            rc = self._lib.flame_init(self._ctx_or_raise(), self._ptr(r), self._ptr(uu), self._ptr(bb),
+                                      self._ptr(gu), self._ptr(gb))
+        _check(rc, "flame_init")
+
+    def step(self, n=1):
+        _check(self._lib.flame_step(self._ctx_or_raise(), int(n)), "flame_step")
+
+    def sync(self):
+        _check(self._lib.flame_sync(self._ctx_or_raise()), "flame_sync")
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(self._lib.flame_info(self._ctx_or_raise(), ctypes.byref(inf)), "flame_info")
+        return dict(step=inf.step, parity=inf.parity, nonfinite=inf.nonfinite, cfl=inf.cfl, max_speed=inf.max_speed)
+
+    def moments(self, out=None) -> dict:
+        """rho, u, B, J of the current pre-collision populations (FP64 CUDA tensors)."""
+        t = self.torch
+        if out is None:
+            out = dict(rho=t.empty(self.shape, dtype=t.float64, device=self.device),
+                       u=t.empty((3,) + self.shape, dtype=t.float64, device=self.device),
+                       B=t.empty((3,) + self.shape, dtype=t.float64, device=self.device),
+                       J=t.empty((3,) + self.shape, dtype=t.float64, device=self.device))
+        _check(self._lib.flame_moments(self._ctx_or_raise(), self._ptr(out.get("rho")), self._ptr(out.get("u")),
+                                       self._ptr(out.get("B")), self._ptr(out.get("J"))), "flame_moments")
+        return out
+
+    def populations(self):
+        """Decoded pre-collision populations [48, nz, ny, nx], FP64, natural slot order."""
+        t = self.torch
+        f = t.empty((48,) + self.shape, dtype=t.float64, device=self.device)
+        _check(self._lib.flame_populations(self._ctx_or_raise(), self._ptr(f)), "flame_populations")
+        return f
+
+    def reduce(self) -> dict:
+        h = (ctypes.c_double * NSCALARS)()
+        rc = self._lib.flame_reduce(self._ctx_or_raise(), h)
+        vals = dict(zip(SCALAR_NAMES, list(h)))
+        if rc not in (FLAME_OK, FLAME_ERR_NONFINITE):
+            _check(rc, "flame_reduce")
+        vals["status"] = rc
+        return vals
+
+    def spectra(self, nshell):
+        Eu = (ctypes.c_double * nshell)()
+        Eb = (ctypes.c_double * nshell)()
+        _check(self._lib.flame_spectra(self._ctx_or_raise(), int(nshell), Eu, Eb), "flame_spectra")
+        return np.array(Eu[:]), np.array(Eb[:])
+
+    def get_state(self):
+        dst = self.torch.empty_like(self.state)
+        step = ctypes.c_longlong()
+        par = ctypes.c_int()
+        _check(self._lib.flame_get_state(self._ctx_or_raise(), self._ptr(dst), ctypes.byref(step), ctypes.byref(par)),
+               "flame_get_state")
+        return dst, int(step.value), int(par.value)
+
+    def set_state(self, src, step, parity):
+        if src.numel() != self.state.numel() or src.dtype != self.state.dtype:
+            raise ValueError("state blob does not match these parameters")
+        _check(self._lib.flame_set_state(self._ctx_or_raise(), self._ptr(src.contiguous()), int(step), int(parity)),
+               "flame_set_state")
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None:
+            self._lib.flame_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

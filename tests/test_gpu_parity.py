@@ -1,0 +1,230 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances.  The GPU stores populations as deviations from the rest
+equilibrium divided by the lattice weight and collides in FP32; one step
+therefore adds a relative error of order 2^-24 ~ 6e-8 of the dynamic part
+of each population, which grows at most linearly (and in practice like a
+random walk) with the number of steps.  Population tolerances below are
+stated relative to ||f_oracle - f_rest||, the size of the dynamic part:
+1e-6 for up to 20 FP32 steps.  Field tolerances for the 200-step wave are
+the ones the method's accuracy budget allows (1e-5 relative L2).  FP16 and
+BF16 storage round each stored deviation to 11 and 8 significant bits;
+their per-field tolerances (2e-2, 1e-1 at 100 steps) are stated in the
+tests.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import rel_dev_err, rel_l2, rest_populations, run_both, turbulence
+
+pytestmark = pytest.mark.gpu
+
+
+def test_init_matches_oracle_ragged_grid():
+    """Initial populations (FP64 fields -> stored deviations) on a grid with
+    two x tiles and a ragged tail, with a mean field."""
+    shape = (5, 6, 150)
+    u, B = turbulence(shape, 11, 0.04)
+    Bref = (0.02, -0.03, 0.05)
+    B = B + np.array(Bref)[:, None, None, None]
+    fg, mg, fo, mo = run_both(shape, 0.6, 0.55, 1.5, u, B, 0, Bref=Bref)
+    rest = rest_populations(shape, 1.0, Bref)
+    assert rel_dev_err(fg, fo, rest) < 1e-7
+    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-9
+    assert rel_l2(mg["u"], mo["u"]) < 1e-7 and rel_l2(mg["J"], mo["J"]) < 1e-6
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 150), (7, 9, 33), (4, 3, 1), (1, 1, 40), (16, 1, 1)])
+def test_step_fp32_matches_oracle(shape):
+    """20 FP32 steps of the fused kernel (both AA parities, periodic wrap on
+    every face, ragged x tiles, degenerate 1-site axes) vs the literal FP64 oracle."""
+    u, B = turbulence(shape, 3, 0.05)
+    Bref = (0.0, 0.0, 0.08)
+    B = B + np.array(Bref)[:, None, None, None]
+    fg, mg, fo, mo = run_both(shape, 0.56, 0.62, 2.0, u, B, 20, Bref=Bref)
+    rest = rest_populations(shape, 1.0, Bref)
+    assert rel_dev_err(fg, fo, rest, slice(0, 27)) < 1e-6
+    assert rel_dev_err(fg, fo, rest, slice(27, 48)) < 1e-6
+    for k in ("u", "B", "J"):
+        ref = mo[k] - (np.array(Bref)[:, None, None, None] if k == "B" else 0.0)
+        got = mg[k] - (np.array(Bref)[:, None, None, None] if k == "B" else 0.0)
+        assert rel_l2(got, ref) < 1e-6, k
+    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-8
+
+
+def test_step_odd_count_and_ideal_limit():
+    """An odd number of steps (state left in the neighbour-pushed AA layout)
+    and d_i = 0."""
+    shape = (8, 8, 40)
+    u, B = turbulence(shape, 5, 0.05)
+    fg, mg, fo, mo = run_both(shape, 0.52, 0.7, 0.0, u, B, 7)
+    rest = rest_populations(shape)
+    assert rel_dev_err(fg, fo, rest) < 1e-6
+
+
+def test_wave_config1_fp32():
+    """Config 1: 32^3, rho0 = 1, B0 = 0.1 z, d_i = 2, tau_nu = tau_eta = 0.6,
+    circularly polarised wave of amplitude 1e-3 (k = 2 pi/32 along z),
+    200 steps; GPU FP32 vs oracle FP64 per field, and both vs the exact
+    damped Hall-MHD wave."""
+    from oracle import exact_wave as X
+    from paper_2212_11024_gb300 import inputs as I
+    N = 32
+    shape = (N, N, N)
+    k = 2 * np.pi / N
+    ap, _ = X.alpha_pm(k, 2.0)
+    u, B = I.parallel_wave(shape, 1, 1e-3, 0.1, ap)
+    gu, gB = I.parallel_wave_gradients(shape, 1, 1e-3, ap)
+    fg, mg, fo, mo = run_both(shape, 0.6, 0.6, 2.0, u, B, 200, gradu=gu, gradB=gB, Bref=(0, 0, 0.1), literal=False)
+    bz = np.array([0, 0, 0.1])[:, None, None, None]
+    assert rel_l2(mg["u"], mo["u"]) < 1e-5
+    assert rel_l2(mg["B"] - bz, mo["B"] - bz) < 1e-5
+    assert rel_l2(mg["J"], mo["J"]) < 1e-5
+    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-9
+    ue, Be = X.fields(200, shape, 1, 0.1, (0.6 - 0.5) / 3, (0.6 - 0.5) / 4, 2.0, 1e-3, ap * 1e-3)
+    assert rel_l2(mg["u"], ue) < 3.5e-2 and rel_l2(mg["B"] - bz, Be - bz) < 5e-2
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-2), ("bf16", 1e-1)])
+def test_reduced_storage_vs_oracle(storage, tol):
+    """FP16 / BF16 deviation storage with FP32 collision, 100 steps of
+    shell-limited turbulence (rms 0.05, tau 0.51), per-field relative L2
+    against the FP64 oracle."""
+    shape = (24, 24, 24)
+    u, B = turbulence(shape, 9, 0.05, shells=(1, 4))
+    fg, mg, fo, mo = run_both(shape, 0.51, 0.51, 0.05 * 24, u, B, 100, storage=storage, literal=False)
+    for k in ("u", "B", "J"):
+        assert rel_l2(mg[k], mo[k]) < tol, (k, rel_l2(mg[k], mo[k]))
+    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-3
+
+
+def test_reduce_and_spectra_match_oracle():
+    """FP64 diagnostics: scalars and shell spectra of the GPU state vs numpy
+    evaluations of the oracle's fields after the same 10 steps."""
+    from oracle import spectra as S
+    from paper_2212_11024_gb300 import Flame
+    shape = (16, 20, 24)
+    u, B = turbulence(shape, 21, 0.04, shells=(1, 3))
+    B = B + np.array([0.01, 0.0, 0.05])[:, None, None, None]
+    nz, ny, nx = shape
+    sim = Flame(nx, ny, nz, 0.55, 0.57, 1.0, B_ref=(0.01, 0.0, 0.05))
+    sim.init(None, u, B)
+    sim.step(10)
+    sc = sim.reduce()
+    Eu, Eb = sim.spectra(20)
+    sim.close()
+    p = O.Params(nx, ny, nz, 0.55, 0.57, 1.0)
+    pop = O.init(p, None, u, B)
+    O.step(p, pop, 10, literal=False)
+    m = O.moments(p, pop)
+    ref = S.scalars(m["rho"], m["u"], m["B"], m["J"])
+    assert abs(sc["mass"] - ref["mass"]) < 1e-9 * ref["mass"]
+    for a, ax in enumerate("xyz"):
+        assert abs(sc["B_" + ax] - ref["B_mean"][a]) < 1e-9
+    for k in ("E_u", "E_B", "J2"):
+        assert abs(sc[k] - ref[k]) < 1e-5 * ref[k], k
+    assert abs(sc["H_c"] - ref["H_c"]) < 1e-5 * np.sqrt(ref["E_u"] * ref["E_B"]) * 2
+    assert sc["nonfinite"] == 0
+    Eu_ref = S.shell_spectrum(m["u"], 20)
+    Eb_ref = S.shell_spectrum(m["B"] - m["B"].reshape(3, -1).mean(axis=1)[:, None, None, None], 20)
+    big = Eu_ref > 1e-6 * Eu_ref.max()
+    assert np.allclose(Eu[big], Eu_ref[big], rtol=1e-5)
+    big = Eb_ref > 1e-6 * Eb_ref.max()
+    assert np.allclose(Eb[big], Eb_ref[big], rtol=1e-5)
+    # Parseval: all shells together hold the energies
+    assert abs(Eu.sum() - sc["E_u"]) < 1e-6 * sc["E_u"]
+
+
+def test_state_roundtrip_and_resume():
+    """flame_get_state / flame_set_state: stepping 6, saving, stepping 5,
+    restoring and stepping 5 again gives bit-identical populations."""
+    from paper_2212_11024_gb300 import Flame
+    shape = (8, 9, 10)
+    u, B = turbulence(shape, 2, 0.05)
+    sim = Flame(10, 9, 8, 0.6, 0.6, 1.0, storage="fp16")
+    sim.init(None, u, B)
+    sim.step(6)
+    blob, step, par = sim.get_state()
+    assert (step, par) == (6, 0)
+    sim.step(5)
+    a = sim.populations().cpu().numpy()
+    sim.set_state(blob, step, par)
+    sim.step(5)
+    b = sim.populations().cpu().numpy()
+    assert sim.info()["step"] == 11 and sim.info()["parity"] == 1
+    sim.close()
+    assert np.array_equal(a, b)
+
+
+def test_nonfinite_detection_and_cfl_check():
+    """A NaN population planted in a host-built state blob is caught by the
+    step kernel's flag (FLAME_ERR_NONFINITE at the next sync); the strict
+    whistler CFL check rejects pi d_i V_A > 1 at init."""
+    import torch
+    from paper_2212_11024_gb300 import Flame, FlameError
+    from paper_2212_11024_gb300.flame import FLAME_ERR_CFL, FLAME_ERR_NONFINITE
+    shape = (6, 6, 6)
+    u, B = turbulence(shape, 4, 0.02)
+    sim = Flame(6, 6, 6, 0.6, 0.6, 1.0, check_every=0)
+    sim.init(None, u, B)
+    blob, step, par = sim.get_state()
+    f32 = blob.view(torch.float32).clone()
+    f32[5 * 216 + 100] = float("nan")
+    sim.set_state(f32.view(torch.uint8), step, par)
+    sim.step(2)
+    with pytest.raises(FlameError) as e:
+        sim.sync()
+    assert e.value.status == FLAME_ERR_NONFINITE
+    sim.close()
+    B2 = B.copy()
+    B2[2] += 0.5  # V_A = 0.5: pi * 1.0 * 0.5 > 1
+    sim = Flame(6, 6, 6, 0.6, 0.6, 1.0, strict_cfl=True)
+    with pytest.raises(FlameError) as e:
+        sim.init(None, u, B2)
+    assert e.value.status == FLAME_ERR_CFL
+    assert sim.info()["cfl"] > 1.0
+    sim.close()
+
+
+def test_full_size_sampled_sites_256():
+    """256^3 FP16 turbulence (the benchmark configuration, d_i = 12.8,
+    tau = 0.51), launched exactly as the benchmark does: one step of the
+    fused kernel, then the oracle's collision of the GPU's own pre-step
+    populations at 64 sampled sites, streamed, compared with the GPU's
+    post-step populations there.  Global mass and mean field are checked
+    over 4 steps."""
+    from paper_2212_11024_gb300 import Flame
+    import torch
+    N = 256
+    u, B = turbulence((N, N, N), 3, 0.05, shells=(1, 4))
+    sim = Flame(N, N, N, 0.51, 0.51, 0.05 * N, storage="fp16")
+    sim.init(None, u, B)
+    del u, B
+    sim.step(1)
+    f0 = sim.populations()  # pre-collision at t = 1 (odd parity)
+    s0 = sim.reduce()
+    sim.step(1)
+    f1 = sim.populations()
+    rng = np.random.default_rng(0)
+    C, _, XI, _ = O.lattice()
+    vel = np.concatenate([C, XI, XI, XI])
+    worst = 0.0
+    for _ in range(64):
+        z, y, x = rng.integers(0, N, 3)
+        pre = f0[:, z, y, x].cpu().numpy()
+        post, _ = O.site_collide(pre, 0.51, 0.51, 0.05 * N, literal=True)
+        idx = [((z + c[2]) % N, (y + c[1]) % N, (x + c[0]) % N) for c in vel]
+        got = np.array([float(f1[q, i[0], i[1], i[2]]) for q, i in enumerate(idx)])
+        rest = rest_populations((1, 1, 1))[:, 0, 0, 0]
+        worst = max(worst, np.abs(got - post).max() / np.abs(post - rest).max())
+    # FP16 storage of the result: 2^-11 relative to the dynamic part
+    assert worst < 2e-3, worst
+    del f0, f1
+    torch.cuda.empty_cache()
+    sim.step(2)
+    s1 = sim.reduce()
+    assert abs(s1["mass"] - s0["mass"]) < 1e-3 * N ** 3 * 1e-3
+    for ax in "xyz":
+        assert abs(s1["B_" + ax] - s0["B_" + ax]) < 1e-5
+    sim.close()
