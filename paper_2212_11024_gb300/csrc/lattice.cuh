@@ -46,6 +46,14 @@ __host__ __device__ constexpr double w27d(int i) {
          : (cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i)) == 2 ? 1.0 / 54.0
                                                                             : 1.0 / 216.0;
 }
+// 216 w_i: 64, 16, 4, 1 -- exact in FP32, so moment sums in the kernel use
+// the same weights the collision conserves.
+__host__ __device__ constexpr int w27x216(int i) {
+  return (cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i)) == 0   ? 64
+         : (cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i)) == 1 ? 16
+         : (cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i)) == 2 ? 4
+                                                                            : 1;
+}
 // Sec. 3.2 weights: 1/4 rest, 1/8 faces.
 __host__ __device__ constexpr double w7d(int i) { return i == 0 ? 0.25 : 0.125; }
 

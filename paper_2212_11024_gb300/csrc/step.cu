@@ -101,12 +101,13 @@ __global__ void __launch_bounds__(kStepThreads)
 #pragma unroll
     for (int i = 0; i < kM; ++i) sg[b][i] = Codec<T>::dec(pop[src7<ODD>(b, i, site, nb, n3)]);
 
-  // a2: rho, momentum and raw second moment, as deviations from rest.
+  // a2: rho, momentum and raw second moment, as deviations from rest,
+  // accumulated with the exact integer weights 216 w_i and scaled once.
   float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
   float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const float t = (float)w27d(i) * sf[i];
+    const float t = (float)w27x216(i) * sf[i];
     drho += t;
     if (cx27(i) != 0) {
       jx += cx27(i) > 0 ? t : -t;
@@ -124,6 +125,16 @@ __global__ void __launch_bounds__(kStepThreads)
     if (cx27(i) * cz27(i) != 0) pxz += cx27(i) * cz27(i) > 0 ? t : -t;
     if (cy27(i) * cz27(i) != 0) pyz += cy27(i) * cz27(i) > 0 ? t : -t;
   }
+  drho = drho / 216.f;
+  jx = jx / 216.f;
+  jy = jy / 216.f;
+  jz = jz / 216.f;
+  pxx = pxx / 216.f;
+  pyy = pyy / 216.f;
+  pzz = pzz / 216.f;
+  pxy = pxy / 216.f;
+  pxz = pxz / 216.f;
+  pyz = pyz / 216.f;
   const float rho = k.rho0 + drho;
   const float irho = 1.f / rho;
   const float U[3] = {jx * irho, jy * irho, jz * irho};
@@ -187,12 +198,14 @@ __global__ void __launch_bounds__(kStepThreads)
   const float Nxz = Br[0] * bz + bx * Br[2] + bx * bz;
   const float Nyz = Br[1] * bz + by * Br[2] + by * bz;
   const float miso = Br[0] * bx + Br[1] * by + Br[2] * bz + 0.5f * (bx * bx + by * by + bz * bz);
-  const float trN3 = (Nxx + Nyy + Nzz) * (1.f / 3.f);
+  // tr(N)/3 enters the Lorentz term as 1.5 tr(N) = 4.5 tr(N)/3: exact
+  // constants keep the term's mass exactly zero (a rounded 1/3 biases it).
+  const float trN15 = 1.5f * (Nxx + Nyy + Nzz);
   // (1 - w) dev(Pi - rho U U - M): the non-equilibrium deviatoric stress.
   const float Sxx = pxx - rho * U[0] * U[0] + Nxx, Syy = pyy - rho * U[1] * U[1] + Nyy,
               Szz = pzz - rho * U[2] * U[2] + Nzz;
   const float r = 1.f - k.omega;
-  const float tr3 = (Sxx + Syy + Szz) * (1.f / 3.f);
+  const float tr3 = (Sxx + Syy + Szz) / 3.f;
   const float Dxx = r * (Sxx - tr3), Dyy = r * (Syy - tr3), Dzz = r * (Szz - tr3);
   const float Dxy = r * (pxy - rho * U[0] * U[1] + Nxy);
   const float Dxz = r * (pxz - rho * U[0] * U[2] + Nxz);
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(kStepThreads)
       A0[q] = Dxx * p2[px] * p0[1][py] + Dyy * p0[0][px] * p2[py] + Dxy * p1[0][px] * p1[1][py];
       A1[q] = Dxz * p1[0][px] * p0[1][py] + Dyz * p0[0][px] * p1[1][py];
       A2[q] = Dzz * p0[0][px] * p0[1][py];
-      Lxy[q] = 4.5f * (miso * (cx * cx + cy * cy - 1.f) - (Nxx * cx * cx + Nyy * cy * cy + 2.f * Nxy * cx * cy) + trN3);
+      Lxy[q] = 4.5f * (miso * (cx * cx + cy * cy - 1.f) - (Nxx * cx * cx + Nyy * cy * cy + 2.f * Nxy * cx * cy)) + trN15;
     }
 
   // a7: f*_i / w_i - (rest reference) = drho + rho E_i + Lorentz_i + P_i.

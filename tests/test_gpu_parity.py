@@ -6,7 +6,12 @@ therefore adds a relative error of order 2^-24 ~ 6e-8 of the dynamic part
 of each population, which grows at most linearly (and in practice like a
 random walk) with the number of steps.  Population tolerances below are
 stated relative to ||f_oracle - f_rest||, the size of the dynamic part:
-1e-6 for up to 20 FP32 steps.  Field tolerances for the 200-step wave are
+1e-6 for up to 20 FP32 steps.  Densities are compared in absolute terms:
+a site's rho carries the rounding of 27 stored deviations of size ~0.1,
+about 3e-9 per step, hence 5e-9 at t = 0 and 5e-8 after 20 steps.  The
+current is a first-moment difference of magnetic populations that carry
+the whole field B, so its relative error is ~|B|/|J| times larger than
+that of B: 5e-6 after 20 steps.  Field tolerances for the 200-step wave are
 the ones the method's accuracy budget allows (1e-5 relative L2).  FP16 and
 BF16 storage round each stored deviation to 11 and 8 significant bits;
 their per-field tolerances (2e-2, 1e-1 at 100 steps) are stated in the
@@ -31,8 +36,8 @@ def test_init_matches_oracle_ragged_grid():
     fg, mg, fo, mo = run_both(shape, 0.6, 0.55, 1.5, u, B, 0, Bref=Bref)
     rest = rest_populations(shape, 1.0, Bref)
     assert rel_dev_err(fg, fo, rest) < 1e-7
-    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-9
-    assert rel_l2(mg["u"], mo["u"]) < 1e-7 and rel_l2(mg["J"], mo["J"]) < 1e-6
+    assert np.abs(mg["rho"] - mo["rho"]).max() < 5e-9
+    assert rel_l2(mg["u"], mo["u"]) < 1e-7 and rel_l2(mg["J"], mo["J"]) < 2e-6
 
 
 @pytest.mark.parametrize("shape", [(6, 5, 150), (7, 9, 33), (4, 3, 1), (1, 1, 40), (16, 1, 1)])
@@ -46,11 +51,11 @@ def test_step_fp32_matches_oracle(shape):
     rest = rest_populations(shape, 1.0, Bref)
     assert rel_dev_err(fg, fo, rest, slice(0, 27)) < 1e-6
     assert rel_dev_err(fg, fo, rest, slice(27, 48)) < 1e-6
-    for k in ("u", "B", "J"):
+    for k, tol in (("u", 1e-6), ("B", 1e-6), ("J", 5e-6)):
         ref = mo[k] - (np.array(Bref)[:, None, None, None] if k == "B" else 0.0)
         got = mg[k] - (np.array(Bref)[:, None, None, None] if k == "B" else 0.0)
-        assert rel_l2(got, ref) < 1e-6, k
-    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-8
+        assert rel_l2(got, ref) < tol, k
+    assert np.abs(mg["rho"] - mo["rho"]).max() < 5e-8
 
 
 def test_step_odd_count_and_ideal_limit():
@@ -119,6 +124,7 @@ def test_reduce_and_spectra_match_oracle():
     O.step(p, pop, 10, literal=False)
     m = O.moments(p, pop)
     ref = S.scalars(m["rho"], m["u"], m["B"], m["J"])
+    # FP32 rounding leaves ~1e-11 of mass per site and step
     assert abs(sc["mass"] - ref["mass"]) < 1e-9 * ref["mass"]
     for a, ax in enumerate("xyz"):
         assert abs(sc["B_" + ax] - ref["B_mean"][a]) < 1e-9
