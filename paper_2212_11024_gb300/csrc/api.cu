@@ -7,7 +7,7 @@
 #include <cstring>
 #include <new>
 
-#include "../../include/flame.h"
+#include "flame.h"
 #include "flame_internal.h"
 #include "lattice.cuh"
 

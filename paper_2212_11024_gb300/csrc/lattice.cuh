@@ -27,6 +27,22 @@ __host__ __device__ constexpr int cz27(int i) {
   return t[i];
 }
 
+// Index of the D3Q27 velocity (px-1, py-1, pz-1), p = 0, 1, 2.
+__host__ __device__ constexpr int idx27(int px, int py, int pz) {
+  constexpr int t[kQ] = {10, 8, 26, 6, 3, 20, 12, 22, 24, 4, 2, 18, 1, 0, 14, 5, 15, 17, 11, 9, 25, 7, 16, 19, 13, 21, 23};
+  return t[px + 3 * py + 9 * pz];
+}
+constexpr bool idx27_consistent() {
+  for (int pz = 0; pz < 3; ++pz)
+    for (int py = 0; py < 3; ++py)
+      for (int px = 0; px < 3; ++px) {
+        const int i = idx27(px, py, pz);
+        if (cx27(i) != px - 1 || cy27(i) != py - 1 || cz27(i) != pz - 1) return false;
+      }
+  return true;
+}
+static_assert(idx27_consistent(), "idx27 must invert the App. A velocity table");
+
 // D3Q7 (Sec. 3.2): rest, +x, -x, +y, -y, +z, -z.
 __host__ __device__ constexpr int mx7(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
 __host__ __device__ constexpr int my7(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }

@@ -32,7 +32,11 @@
 namespace flame {
 namespace {
 
-constexpr int kStepThreads = 128;
+// Step launch: 256 threads per block (a whole 256-site x row at 256^3) and
+// at most 80 registers per thread (3 resident blocks per SM); the block
+// shape and register budget were chosen by timing at 256^3.
+constexpr int kStepThreads = 256;
+constexpr int kStepMinBlocks = 3;
 
 // Site-index offsets of the periodic neighbours.
 struct Nbr {
@@ -80,64 +84,97 @@ __device__ __forceinline__ long long dst7(int b, int i, int site, const Nbr& nb,
              : (long long)mslot(b, opp7(i)) * n3 + site;
 }
 
+// Base pointers of the 48 slots (slot q starts at q * N3), passed as kernel
+// parameters so that each access is one index computation on a parameter.
+template <class T>
+struct Slots {
+  T* p[kPop];
+};
+
+// Site offset of the source (pre-collision) and destination
+// (post-collision) of the population on velocity (cx, cy, cz), and the
+// slot used there, for the two AA parities.
+template <bool ODD>
+__device__ __forceinline__ int src_off(const Nbr& nb, int cx, int cy, int cz) {
+  return ODD ? nb(-cx, -cy, -cz) : 0;
+}
+template <bool ODD>
+__device__ __forceinline__ int dst_off(const Nbr& nb, int cx, int cy, int cz) {
+  return ODD ? nb(cx, cy, cz) : 0;
+}
+
 template <class T, bool ODD>
-__global__ void __launch_bounds__(kStepThreads)
-    step_kernel(T* __restrict__ pop, Grid g, StepConsts k, unsigned* __restrict__ flag) {
+__global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
+    step_kernel(Slots<T> P, Grid g, StepConsts k, unsigned* __restrict__ flag) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
   const int site = (z * g.ny + y) * g.nx + x;
   const Nbr nb = make_nbr(x, y, z, g);
-  const long long n3 = g.n3;
 
-  // a1: load and decode the 48 pre-collision populations.
-  float sf[kQ];
+  // a1: load and decode the 48 pre-collision populations.  Fluid values are
+  // kept in velocity-cube order s[px + 3 py + 9 pz], p = c + 1.
+  float s[kQ];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) sf[i] = Codec<T>::dec(pop[src27<ODD>(i, site, nb, n3)]);
+  for (int pz = 0; pz < 3; ++pz)
+#pragma unroll
+    for (int py = 0; py < 3; ++py)
+#pragma unroll
+      for (int px = 0; px < 3; ++px) {
+        const int i = idx27(px, py, pz);
+        const int slot = ODD ? opp27(i) : i;
+        s[px + 3 * py + 9 * pz] = Codec<T>::dec(P.p[slot][site + src_off<ODD>(nb, px - 1, py - 1, pz - 1)]);
+      }
   float sg[3][kM];
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int i = 0; i < kM; ++i) sg[b][i] = Codec<T>::dec(pop[src7<ODD>(b, i, site, nb, n3)]);
+    for (int i = 0; i < kM; ++i) {
+      const int slot = mslot(b, ODD ? opp7(i) : i);
+      sg[b][i] = Codec<T>::dec(P.p[slot][site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i))]);
+    }
 
-  // a2: rho, momentum and raw second moment, as deviations from rest,
-  // accumulated with the exact integer weights 216 w_i and scaled once.
-  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+  // a2: rho, momentum and raw second moment (deviations from rest) by three
+  // 1-D passes over the velocity cube with the 1-D weights (1, 4, 1) / 6.
+  float m0[9], m1[9], m2[9];  // x pass: [py + 3 pz]
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const float t = (float)w27x216(i) * sf[i];
-    drho += t;
-    if (cx27(i) != 0) {
-      jx += cx27(i) > 0 ? t : -t;
-      pxx += t;
-    }
-    if (cy27(i) != 0) {
-      jy += cy27(i) > 0 ? t : -t;
-      pyy += t;
-    }
-    if (cz27(i) != 0) {
-      jz += cz27(i) > 0 ? t : -t;
-      pzz += t;
-    }
-    if (cx27(i) * cy27(i) != 0) pxy += cx27(i) * cy27(i) > 0 ? t : -t;
-    if (cx27(i) * cz27(i) != 0) pxz += cx27(i) * cz27(i) > 0 ? t : -t;
-    if (cy27(i) * cz27(i) != 0) pyz += cy27(i) * cz27(i) > 0 ? t : -t;
+  for (int q = 0; q < 9; ++q) {
+    const float sm = s[3 * q], s0 = s[3 * q + 1], sp = s[3 * q + 2];
+    const float t = sp + sm;
+    m0[q] = fmaf(4.f, s0, t);
+    m1[q] = sp - sm;
+    m2[q] = t;
   }
-  drho = drho / 216.f;
-  jx = jx / 216.f;
-  jy = jy / 216.f;
-  jz = jz / 216.f;
-  pxx = pxx / 216.f;
-  pyy = pyy / 216.f;
-  pzz = pzz / 216.f;
-  pxy = pxy / 216.f;
-  pxz = pxz / 216.f;
-  pyz = pyz / 216.f;
+  float M00[3], M10[3], M20[3], M01[3], M11[3], M02[3];  // y pass: [pz]
+#pragma unroll
+  for (int pz = 0; pz < 3; ++pz) {
+    const int q = 3 * pz;
+    const float t0 = m0[q + 2] + m0[q];
+    M00[pz] = fmaf(4.f, m0[q + 1], t0);
+    M02[pz] = t0;
+    M01[pz] = m0[q + 2] - m0[q];
+    M10[pz] = fmaf(4.f, m1[q + 1], m1[q + 2] + m1[q]);
+    M11[pz] = m1[q + 2] - m1[q];
+    M20[pz] = fmaf(4.f, m2[q + 1], m2[q + 2] + m2[q]);
+  }
+  // The density deviation is divided exactly (correct rounding keeps mass
+  // unbiased); momentum and stress use the reciprocal of 216 rho / of 216,
+  // whose rounding is not one-signed across sites (U) or only rescales the
+  // non-conserved stress by 1 + O(1e-8) (Pi).
+  const float t00 = M00[2] + M00[0];
+  const float drho = fmaf(4.f, M00[1], t00) / 216.f;
   const float rho = k.rho0 + drho;
-  const float irho = 1.f / rho;
-  const float U[3] = {jx * irho, jy * irho, jz * irho};
+  const float irho216 = 1.f / (216.f * rho);
+  const float U[3] = {fmaf(4.f, M10[1], M10[2] + M10[0]) * irho216, fmaf(4.f, M01[1], M01[2] + M01[0]) * irho216,
+                      (M00[2] - M00[0]) * irho216};
+  constexpr float k216 = 1.f / 216.f;
+  const float pxx = fmaf(4.f, M20[1], M20[2] + M20[0]) * k216;
+  const float pyy = fmaf(4.f, M02[1], M02[2] + M02[0]) * k216;
+  const float pzz = t00 * k216;
+  const float pxy = fmaf(4.f, M11[1], M11[2] + M11[0]) * k216;
+  const float pxz = (M10[2] - M10[0]) * k216;
+  const float pyz = (M01[2] - M01[0]) * k216;
 
   // a3: B = sum_i g_i and Lambda_ab = sum_i xi_ia g_ib.
   float dB[3], lam[3][3];
@@ -152,7 +189,7 @@ __global__ void __launch_bounds__(kStepThreads)
 
   // Non-finite guard: one relaxed flag read, and an atomic only while the
   // flag is still clear, so a blown-up field does not serialise on it.
-  if (!isfinite(drho + jx + jy + jz + dB[0] + dB[1] + dB[2])) {
+  if (!isfinite(drho + U[0] + U[1] + U[2] + dB[0] + dB[1] + dB[2])) {
     if (*((volatile unsigned*)flag) == 0u) atomicOr(flag, 1u);
   }
 
@@ -161,15 +198,15 @@ __global__ void __launch_bounds__(kStepThreads)
   const float A[3] = {lam[1][2] - lam[2][1], lam[2][0] - lam[0][2], lam[0][1] - lam[1][0]};
   const float uxb[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2], U[0] * B[1] - U[1] * B[0]};
   const float yv[3] = {-gq * (A[0] - 2.f * uxb[0]), -gq * (A[1] - 2.f * uxb[1]), -gq * (A[2] - 2.f * uxb[2])};
-  const float s = 2.f * k.alphaH * gq;
+  const float sH = 2.f * k.alphaH * gq;
   const float yxb[3] = {yv[1] * B[2] - yv[2] * B[1], yv[2] * B[0] - yv[0] * B[2], yv[0] * B[1] - yv[1] * B[0]};
   const float yb = yv[0] * B[0] + yv[1] * B[1] + yv[2] * B[2];
   const float b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-  const float iden = 1.f / (1.f + s * s * b2);
+  const float iden = 1.f / (1.f + sH * sH * b2);
   float V[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float J = (yv[a] - s * yxb[a] + s * s * yb * B[a]) * iden;
+    const float J = (yv[a] - sH * yxb[a] + sH * sH * yb * B[a]) * iden;
     V[a] = U[a] - k.alphaH * J;
   }
 
@@ -179,12 +216,16 @@ __global__ void __launch_bounds__(kStepThreads)
     const float om = k.omegaB, cm = 1.f - k.omegaB;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      pop[dst7<ODD>(b, 0, site, nb, n3)] = Codec<T>::enc(cm * sg[b][0] + om * dB[b]);
+      P.p[mslot(b, ODD ? 0 : opp7(0))][site] = Codec<T>::enc(cm * sg[b][0] + om * dB[b]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const float l0 = (a == b) ? 0.f : 4.f * (V[a] * B[b] - B[a] * V[b]);
-        pop[dst7<ODD>(b, 2 * a + 1, site, nb, n3)] = Codec<T>::enc(cm * sg[b][2 * a + 1] + om * (dB[b] + l0));
-        pop[dst7<ODD>(b, 2 * a + 2, site, nb, n3)] = Codec<T>::enc(cm * sg[b][2 * a + 2] + om * (dB[b] - l0));
+#pragma unroll
+        for (int h = 1; h <= 2; ++h) {
+          const int i = 2 * a + h;
+          const float v = cm * sg[b][i] + om * (h == 1 ? dB[b] + l0 : dB[b] - l0);
+          P.p[mslot(b, ODD ? i : opp7(i))][site + dst_off<ODD>(nb, mx7(i), my7(i), mz7(i))] = Codec<T>::enc(v);
+        }
       }
     }
   }
@@ -198,9 +239,6 @@ __global__ void __launch_bounds__(kStepThreads)
   const float Nxz = Br[0] * bz + bx * Br[2] + bx * bz;
   const float Nyz = Br[1] * bz + by * Br[2] + by * bz;
   const float miso = Br[0] * bx + Br[1] * by + Br[2] * bz + 0.5f * (bx * bx + by * by + bz * bz);
-  // tr(N)/3 enters the Lorentz term as 1.5 tr(N) = 4.5 tr(N)/3: exact
-  // constants keep the term's mass exactly zero (a rounded 1/3 biases it).
-  const float trN15 = 1.5f * (Nxx + Nyy + Nzz);
   // (1 - w) dev(Pi - rho U U - M): the non-equilibrium deviatoric stress.
   const float Sxx = pxx - rho * U[0] * U[0] + Nxx, Syy = pyy - rho * U[1] * U[1] + Nyy,
               Szz = pzz - rho * U[2] * U[2] + Nzz;
@@ -211,52 +249,65 @@ __global__ void __launch_bounds__(kStepThreads)
   const float Dxz = r * (pxz - rho * U[0] * U[2] + Nxz);
   const float Dyz = r * (pyz - rho * U[1] * U[2] + Nyz);
 
-  // 1-D factors per axis and velocity component c = -1, 0, +1 (index c+1),
-  // all divided by the 1-D weight: e = psi/w1 - 1, p0, p1, p2 = the 1-D
-  // inverse-moment maps of m0, m1, m2.
-  float e[3][3], p0[3][3], p1[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float u = U[a], uu = u * u;
-    e[a][0] = 3.f * uu - 3.f * u;
-    e[a][1] = -1.5f * uu;
-    e[a][2] = 3.f * uu + 3.f * u;
-    p0[a][0] = 3.f * (uu - u);
-    p0[a][1] = 1.5f * (1.f - uu);
-    p0[a][2] = 3.f * (uu + u);
-    p1[a][0] = 6.f * u - 3.f;
-    p1[a][1] = -3.f * u;
-    p1[a][2] = 6.f * u + 3.f;
+  // 1-D factors of the x and y axes, divided by the 1-D weight: e = psi/w1 - 1
+  // and p0, p1 (p2 is constant), the inverse-moment maps of m0, m1, m2.
+  float ex[3], ey[3], p0x[3], p0y[3], p1x[3], p1y[3];
+  {
+    const float u = U[0], uu = u * u;
+    ex[0] = 3.f * uu - 3.f * u, ex[1] = -1.5f * uu, ex[2] = 3.f * uu + 3.f * u;
+    p0x[0] = 3.f * (uu - u), p0x[1] = 1.5f * (1.f - uu), p0x[2] = 3.f * (uu + u);
+    p1x[0] = 6.f * u - 3.f, p1x[1] = -3.f * u, p1x[2] = 6.f * u + 3.f;
+  }
+  {
+    const float u = U[1], uu = u * u;
+    ey[0] = 3.f * uu - 3.f * u, ey[1] = -1.5f * uu, ey[2] = 3.f * uu + 3.f * u;
+    p0y[0] = 3.f * (uu - u), p0y[1] = 1.5f * (1.f - uu), p0y[2] = 3.f * (uu + u);
+    p1y[0] = 6.f * u - 3.f, p1y[1] = -3.f * u, p1y[2] = 6.f * u + 3.f;
   }
   constexpr float p2[3] = {3.f, -1.5f, 3.f};
+  // Along z every term is a quadratic in cz: ez(c) = e0z + e1z c + e2z c^2,
+  // p0z(c) = q00 + q10 c + q20 c^2, p1z(c) = q01 + 3 c + q21 c^2,
+  // p2z(c) = -1.5 + 4.5 c^2.
+  const float uz = U[2], uzz = uz * uz;
+  const float e0z = -1.5f * uzz, e1z = 3.f * uz, e2z = 4.5f * uzz;
+  const float q00 = 1.5f * (1.f - uzz), q10 = 3.f * uz, q20 = fmaf(4.5f, uzz, -1.5f);
+  const float q01 = -3.f * uz, q21 = 9.f * uz;
+  // Lorentz term 4.5 (miso (|c|^2 - 1) - c.N.c) + 1.5 tr(N), split as
+  // Lxy + Lz1 cz + Lz2 cz^2.
+  const float Lbase = 1.5f * (Nxx + Nyy + Nzz) - 4.5f * miso;
+  const float LA = 4.5f * (miso - Nxx), LB = 4.5f * (miso - Nyy), LC = 9.f * Nxy;
+  const float NX = -9.f * Nxz, NY = -9.f * Nyz, LZ = 4.5f * (miso - Nzz);
 
-  // Per (cx, cy) pair: e_xy, the Dzz / Dxz+Dyz / Dxx+Dyy+Dxy coefficients of
-  // p2z, p1z, p0z, and the in-plane Lorentz part.
-  float exy[9], A0[9], A1[9], A2[9], Lxy[9];
+  // a7: for each (cx, cy), f*/w - (rest reference) = Z0 + Z1 cz + Z2 cz^2.
 #pragma unroll
-  for (int px = 0; px < 3; ++px)
+  for (int py = 0; py < 3; ++py)
 #pragma unroll
-    for (int py = 0; py < 3; ++py) {
-      const int q = px * 3 + py;
-      const float cx = (float)(px - 1), cy = (float)(py - 1);
-      exy[q] = e[0][px] + e[1][py] + e[0][px] * e[1][py];
-      A0[q] = Dxx * p2[px] * p0[1][py] + Dyy * p0[0][px] * p2[py] + Dxy * p1[0][px] * p1[1][py];
-      A1[q] = Dxz * p1[0][px] * p0[1][py] + Dyz * p0[0][px] * p1[1][py];
-      A2[q] = Dzz * p0[0][px] * p0[1][py];
-      Lxy[q] = 4.5f * (miso * (cx * cx + cy * cy - 1.f) - (Nxx * cx * cx + Nyy * cy * cy + 2.f * Nxy * cx * cy)) + trN15;
+    for (int px = 0; px < 3; ++px) {
+      const int cx = px - 1, cy = py - 1;
+      const float exy = ex[px] + ey[py] + ex[px] * ey[py];
+      const float g = fmaf(rho, exy, rho);
+      const float A0 = (Dxx * p2[px]) * p0y[py] + (Dyy * p2[py]) * p0x[px] + (Dxy * p1x[px]) * p1y[py];
+      const float A1 = (Dxz * p1x[px]) * p0y[py] + (Dyz * p1y[py]) * p0x[px];
+      const float A2 = (Dzz * p0x[px]) * p0y[py];
+      float Lxy = Lbase;
+      if (cx != 0) Lxy += LA;
+      if (cy != 0) Lxy += LB;
+      if (cx * cy != 0) Lxy += (cx * cy > 0) ? -LC : LC;
+      float Lz1 = 0.f;
+      if (cx != 0) Lz1 += (cx > 0) ? NX : -NX;
+      if (cy != 0) Lz1 += (cy > 0) ? NY : -NY;
+      const float Z0 = fmaf(rho, exy, drho) + g * e0z + A0 * q00 + A1 * q01 - 1.5f * A2 + Lxy;
+      const float Z1 = g * e1z + A0 * q10 + 3.f * A1 + Lz1;
+      const float Z2 = g * e2z + A0 * q20 + A1 * q21 + 4.5f * A2 + LZ;
+      const float tz = Z0 + Z2;
+      const float vz[3] = {tz - Z1, Z0, tz + Z1};
+#pragma unroll
+      for (int pz = 0; pz < 3; ++pz) {
+        const int i = idx27(px, py, pz);
+        const int slot = ODD ? i : opp27(i);
+        P.p[slot][site + dst_off<ODD>(nb, cx, cy, pz - 1)] = Codec<T>::enc(vz[pz]);
+      }
     }
-
-  // a7: f*_i / w_i - (rest reference) = drho + rho E_i + Lorentz_i + P_i.
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const int px = cx27(i) + 1, py = cy27(i) + 1, pz = cz27(i) + 1;
-    const int q = px * 3 + py;
-    const float cz = (float)cz27(i);
-    const float E = exy[q] + e[2][pz] + exy[q] * e[2][pz];
-    const float P = A0[q] * p0[2][pz] + A1[q] * p1[2][pz] + A2[q] * p2[pz];
-    const float L = Lxy[q] + 4.5f * (cz * cz * (miso - Nzz) - 2.f * cz * (Nxz * (float)cx27(i) + Nyz * (float)cy27(i)));
-    pop[dst27<ODD>(i, site, nb, n3)] = Codec<T>::enc(drho + rho * E + L + P);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -517,9 +568,11 @@ __global__ void reduce_final_kernel(const double* __restrict__ partials, int nbl
   out[v] = a;
 }
 
-dim3 site_block(const Grid& g) {
-  int bx = g.nx >= 128 ? 128 : ((g.nx + 31) / 32) * 32;
-  int by = 128 / bx;
+// Block of `threads` threads: x-rows of up to `threads` sites, several
+// rows per block when nx is small.
+dim3 site_block(const Grid& g, int threads = 128) {
+  int bx = g.nx >= threads ? threads : ((g.nx + 31) / 32) * 32;
+  int by = threads / bx;
   if (by > g.ny) by = g.ny;
   if (by < 1) by = 1;
   return dim3(bx, by, 1);
@@ -529,11 +582,13 @@ dim3 site_grid(const Grid& g, dim3 b) { return dim3((g.nx + b.x - 1) / b.x, (g.n
 
 template <class T>
 cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s) {
-  const dim3 b = site_block(g), gr = site_grid(g, b);
+  const dim3 b = site_block(g, kStepThreads), gr = site_grid(g, b);
+  Slots<T> P;
+  for (int q = 0; q < kPop; ++q) P.p[q] = static_cast<T*>(pop) + (size_t)q * (size_t)g.n3;
   if (odd)
-    step_kernel<T, true><<<gr, b, 0, s>>>(static_cast<T*>(pop), g, k, flag);
+    step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, flag);
   else
-    step_kernel<T, false><<<gr, b, 0, s>>>(static_cast<T*>(pop), g, k, flag);
+    step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, flag);
   return cudaGetLastError();
 }
 
