@@ -170,6 +170,30 @@ flame_status flame_get_state(flame_ctx *ctx, void *d_dst, long long *step, int *
  * Errors: FLAME_ERR_STATE (parity not 0/1, step < 0).  Asynchronous. */
 flame_status flame_set_state(flame_ctx *ctx, const void *d_src, long long step, int parity);
 
+/* Largest block count flame_reduce_static accepts; its device scratch holds
+ * this many blocks' partial sums (139,264 bytes per device). */
+#define FLAME_STATIC_REDUCE_BLOCKS_MAX 1024
+
+/* flame_reduce without any allocation, for callers that must not call
+ * cudaMalloc (flame_reduce allocates a workspace on its first call, which
+ * can synchronise the device and stall queued work, and some hosts give all
+ * device memory to their own caching allocator).  The paper has no
+ * counterpart; it is a property of this library's interface.
+ * Writes the same FLAME_NSCALARS scalars as flame_reduce, FP64, to device
+ * memory d_scalars (caller-owned), asynchronously on the context's stream;
+ * the non-finite count is in d_scalars[FLAME_S_NONFINITE], not in the
+ * status.  nblocks: reduction blocks, 1..FLAME_STATIC_REDUCE_BLOCKS_MAX, or
+ * 0 for 4 per SM; larger values fail with FLAME_ERR_PARAM.
+ * The partial sums live in a fixed device array that each device holds from
+ * library load until exit.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device made
+ * current): make that first call before any stream capture.  The array is
+ * shared by all contexts on the device and keeps the last call's contents;
+ * every call overwrites what it reads, and calls that overlap on the GPU
+ * race on it.  Errors: FLAME_ERR_PARAM, FLAME_ERR_STATE (no flame_init),
+ * FLAME_ERR_CUDA, sticky context errors. */
+flame_status flame_reduce_static(flame_ctx *ctx, int nblocks, double *d_scalars);
+
 /* Release the context and its internal workspace (not the caller's state). */
 void flame_destroy(flame_ctx *ctx);
 

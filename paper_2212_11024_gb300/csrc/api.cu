@@ -134,6 +134,22 @@ cudaError_t launch_shell_bin(const void* spec, Grid g, int nshell, int zero_mean
 }
 }  // namespace flame
 
+int flame_ctx_view(const flame_ctx* c, flame::CtxView* v) {
+  if (!c || !v) return -1;
+  v->state = c->state;
+  v->storage = c->p.storage;
+  v->parity = c->parity;
+  v->device = c->device;
+  v->nsm = c->nsm;
+  v->initialized = c->initialized ? 1 : 0;
+  v->status = (int)c->sticky;
+  v->stream = c->stream;
+  v->g = c->g;
+  v->k = c->k;
+  for (int a = 0; a < 3; ++a) v->Bref[a] = c->p.B_ref[a];
+  return 0;
+}
+
 extern "C" {
 
 size_t flame_state_bytes(const flame_params* p) {

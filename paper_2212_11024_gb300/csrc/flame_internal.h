@@ -44,7 +44,31 @@ constexpr int kRedBlocksMax = 1024;
 cudaError_t launch_reduce(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
                           double* partials, double* out, cudaStream_t s);
 
+// Only the first stage of launch_reduce: per-block partial sums
+// (kRedVals doubles per block) of the reduce kernel into `partials`.
+cudaError_t launch_reduce_partials(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
+                                   double* partials, cudaStream_t s);
+
+// Read-only view of a context for entry points outside api.cu.
+struct CtxView {
+  void* state;
+  int storage;
+  int parity;
+  int device;
+  int nsm;
+  int initialized;
+  int status;  // flame_status of the context (sticky errors)
+  cudaStream_t stream;
+  Grid g;
+  StepConsts k;
+  double Bref[3];
+};
+
 cudaError_t launch_shell_bin(const void* spec /* cufftDoubleComplex */, Grid g, int nshell, int zero_mean,
                              double* shells, cudaStream_t s);
 
 }  // namespace flame
+
+struct flame_ctx;
+// Fills *v from the context; returns 0, or -1 for a null context.
+int flame_ctx_view(const flame_ctx* c, flame::CtxView* v);

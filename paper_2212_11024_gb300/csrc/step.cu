@@ -669,6 +669,28 @@ cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, co
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_reduce_partials(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
+                                   double* partials, cudaStream_t s) {
+  if (nblocks < 1) return cudaErrorInvalidValue;
+  switch (storage) {
+    case 1:
+      if (odd) reduce_kernel<float, true><<<nblocks, 256, 0, s>>>(static_cast<const float*>(pop), g, k, partials);
+      else reduce_kernel<float, false><<<nblocks, 256, 0, s>>>(static_cast<const float*>(pop), g, k, partials);
+      break;
+    case 2:
+      if (odd) reduce_kernel<__half, true><<<nblocks, 256, 0, s>>>(static_cast<const __half*>(pop), g, k, partials);
+      else reduce_kernel<__half, false><<<nblocks, 256, 0, s>>>(static_cast<const __half*>(pop), g, k, partials);
+      break;
+    case 3:
+      if (odd) reduce_kernel<__nv_bfloat16, true><<<nblocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(pop), g, k, partials);
+      else reduce_kernel<__nv_bfloat16, false><<<nblocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(pop), g, k, partials);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
                           double* partials, double* out, cudaStream_t s) {
   if (nblocks < 1 || nblocks > kRedBlocksMax) return cudaErrorInvalidValue;

@@ -83,6 +83,7 @@ def _lib():
             "flame_destroy": (None, [vp]),
             "flame_status_string": (ctypes.c_char_p, [i]),
             "flame_lattice": (i, [P(i), P(i)]),
+            "flame_reduce_static": (i, [vp, i, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -228,6 +229,18 @@ class Flame:
             _check(rc, "flame_reduce")
         vals["status"] = rc
         return vals
+
+    def reduce_static(self, nblocks=0, out=None):
+        """flame_reduce_static: the reduce() scalars computed without any
+        allocation in the library, into a FP64 CUDA tensor of NSCALARS
+        entries (returned).  For callers that must not let the library call
+        cudaMalloc; the first call on a device should precede stream capture."""
+        t = self.torch
+        if out is None:
+            out = t.empty(NSCALARS, dtype=t.float64, device=self.device)
+        _check(self._lib.flame_reduce_static(self._ctx_or_raise(), int(nblocks), self._ptr(out)),
+               "flame_reduce_static")
+        return out
 
     def spectra(self, nshell):
         Eu = (ctypes.c_double * nshell)()
