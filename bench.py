@@ -66,7 +66,7 @@ def hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("step.cu", "lattice.cuh", "flame_internal.h"):
+    for f in ("step.cu", "lattice.cuh", "aa.cuh"):
         with open(os.path.join(ROOT, "paper_2212_11024_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

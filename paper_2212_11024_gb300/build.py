@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libflame.so")
-SOURCES = ["step.cu", "api.cu", "reduce_static.cu"]
-HEADERS = ["lattice.cuh", "flame_internal.h"]
+SOURCES = ["step.cu", "diag.cu", "api.cu", "reduce_static.cu"]
+HEADERS = ["lattice.cuh", "aa.cuh", "flame_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,6 +1,5 @@
-// step.cu -- the fused FLAME collide-and-stream step (one thread per site,
-// AA in-place streaming), plus the initialisation, moments and populations
-// kernels that read the same state.
+// step.cu -- the fused FLAME collide-and-stream step: one thread per site,
+// AA in-place streaming over the 48-slot population state.
 //
 // Algebra of the fluid collision.  With S = diag[1,1,1,1,w,w,w,w,w,1,...,1]
 // (eq. collision_matrix) every central moment except the five deviatoric
@@ -26,8 +25,7 @@
 // 3x3 solve), a5 central-moment fluid collision (eq. cm_collision_step),
 // a6 g^Hall(0) (eq. gHall_eq) and BGK (eq. MHD_LBscheme), a7 encode and
 // store (eq. stream, AA pattern).
-#include "flame_internal.h"
-#include "lattice.cuh"
+#include "aa.cuh"
 
 namespace flame {
 namespace {
@@ -37,71 +35,6 @@ namespace {
 // shape and register budget were chosen by timing at 256^3.
 constexpr int kStepThreads = 256;
 constexpr int kStepMinBlocks = 3;
-
-// Site-index offsets of the periodic neighbours.
-struct Nbr {
-  int xm, xp, ym, yp, zm, zp;
-  __device__ __forceinline__ int operator()(int cx, int cy, int cz) const {
-    return (cx < 0 ? xm : (cx > 0 ? xp : 0)) + (cy < 0 ? ym : (cy > 0 ? yp : 0)) +
-           (cz < 0 ? zm : (cz > 0 ? zp : 0));
-  }
-};
-
-__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const Grid& g) {
-  Nbr n;
-  const int plane = g.nx * g.ny;
-  n.xm = x == 0 ? g.nx - 1 : -1;
-  n.xp = x == g.nx - 1 ? -(g.nx - 1) : 1;
-  n.ym = y == 0 ? (g.ny - 1) * g.nx : -g.nx;
-  n.yp = y == g.ny - 1 ? -(g.ny - 1) * g.nx : g.nx;
-  n.zm = z == 0 ? (g.nz - 1) * plane : -plane;
-  n.zp = z == g.nz - 1 ? -(g.nz - 1) * plane : plane;
-  return n;
-}
-
-// AA pattern.  Pre-collision population on velocity c of a site:
-//   even parity: same site, own slot;  odd: site - c, opposite slot.
-// Post-collision population on velocity c:
-//   even: same site, opposite slot;    odd: site + c, own slot.
-template <bool ODD>
-__device__ __forceinline__ long long src27(int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)opp27(i) * n3 + site + nb(-cx27(i), -cy27(i), -cz27(i))
-             : (long long)i * n3 + site;
-}
-template <bool ODD>
-__device__ __forceinline__ long long dst27(int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))
-             : (long long)opp27(i) * n3 + site;
-}
-template <bool ODD>
-__device__ __forceinline__ long long src7(int b, int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)mslot(b, opp7(i)) * n3 + site + nb(-mx7(i), -my7(i), -mz7(i))
-             : (long long)mslot(b, i) * n3 + site;
-}
-template <bool ODD>
-__device__ __forceinline__ long long dst7(int b, int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))
-             : (long long)mslot(b, opp7(i)) * n3 + site;
-}
-
-// Base pointers of the 48 slots (slot q starts at q * N3), passed as kernel
-// parameters so that each access is one index computation on a parameter.
-template <class T>
-struct Slots {
-  T* p[kPop];
-};
-
-// Site offset of the source (pre-collision) and destination
-// (post-collision) of the population on velocity (cx, cy, cz), and the
-// slot used there, for the two AA parities.
-template <bool ODD>
-__device__ __forceinline__ int src_off(const Nbr& nb, int cx, int cy, int cz) {
-  return ODD ? nb(-cx, -cy, -cz) : 0;
-}
-template <bool ODD>
-__device__ __forceinline__ int dst_off(const Nbr& nb, int cx, int cy, int cz) {
-  return ODD ? nb(cx, cy, cz) : 0;
-}
 
 template <class T, bool ODD>
 __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
@@ -310,275 +243,6 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Initialisation (FP64 arithmetic, once per run).
-
-__device__ __forceinline__ double cdiff(const double* F, int a, int x, int y, int z, const Grid& g) {
-  int xp = x, xm = x, yp = y, ym = y, zp = z, zm = z;
-  if (a == 0) {
-    xp = x + 1 == g.nx ? 0 : x + 1;
-    xm = x == 0 ? g.nx - 1 : x - 1;
-  } else if (a == 1) {
-    yp = y + 1 == g.ny ? 0 : y + 1;
-    ym = y == 0 ? g.ny - 1 : y - 1;
-  } else {
-    zp = z + 1 == g.nz ? 0 : z + 1;
-    zm = z == 0 ? g.nz - 1 : z - 1;
-  }
-  return 0.5 * (F[((long long)zp * g.ny + yp) * g.nx + xp] - F[((long long)zm * g.ny + ym) * g.nx + xm]);
-}
-
-template <class T>
-__global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq, const double* __restrict__ rho_f,
-                            const double* __restrict__ u, const double* __restrict__ Bf,
-                            const double* __restrict__ gu, const double* __restrict__ gB,
-                            unsigned* __restrict__ speed_bits) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
-  const long long n3 = g.n3;
-  const long long site = ((long long)z * g.ny + y) * g.nx + x;
-  const double rho = rho_f ? rho_f[site] : 1.0;
-  const double U[3] = {u[site], u[n3 + site], u[2 * n3 + site]};
-  const double B[3] = {Bf[site], Bf[n3 + site], Bf[2 * n3 + site]};
-  double du[9], dB[9];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      du[3 * a + b] = gu ? gu[(3 * a + b) * n3 + site] : cdiff(u + b * n3, a, x, y, z, g);
-      dB[3 * a + b] = gB ? gB[(3 * a + b) * n3 + site] : cdiff(Bf + b * n3, a, x, y, z, g);
-    }
-  const double J0[3] = {dB[5] - dB[7], dB[6] - dB[2], dB[1] - dB[3]};  // curl B
-  const double omega = (double)k.omega, omegaB = (double)k.omegaB, aH = (double)k.alphaH;
-  const double Br[3] = {(double)k.Bref[0], (double)k.Bref[1], (double)k.Bref[2]};
-  const double b[3] = {B[0] - Br[0], B[1] - Br[1], B[2] - Br[2]};
-  double N[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) N[a][c] = Br[a] * b[c] + b[a] * Br[c] + b[a] * b[c];
-  const double miso = Br[0] * b[0] + Br[1] * b[1] + Br[2] * b[2] + 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-  const double trN3 = (N[0][0] + N[1][1] + N[2][2]) / 3.0;
-  double Pn[3][3];  // first-order non-equilibrium stress -(rho cs^2/omega)(du + du^T)
-  for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) Pn[a][c] = noneq ? -(rho / (3.0 * omega)) * (du[3 * a + c] + du[3 * c + a]) : 0.0;
-  const double trPn3 = (Pn[0][0] + Pn[1][1] + Pn[2][2]) / 3.0;
-  const double drho = rho - (double)k.rho0;
-#pragma unroll 1
-  for (int i = 0; i < kQ; ++i) {
-    const int c[3] = {cx27(i), cy27(i), cz27(i)};
-    double E = 0.0;  // prod(psi/w1) - 1, accumulated stably
-    for (int a = 0; a < 3; ++a) {
-      const double uu = U[a] * U[a];
-      const double ea = c[a] == 0 ? -1.5 * uu : 3.0 * uu + 3.0 * c[a] * U[a];
-      E = E + ea + E * ea;
-    }
-    double cNc = 0.0, cPc = 0.0;
-    for (int a = 0; a < 3; ++a)
-      for (int d = 0; d < 3; ++d) {
-        cNc += c[a] * c[d] * N[a][d];
-        cPc += c[a] * c[d] * Pn[a][d];
-      }
-    const double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-    const double L = 4.5 * (miso * (c2 - 1.0) - cNc + trN3);
-    const double ne = 4.5 * (cPc - trPn3);
-    pop[(long long)i * n3 + site] = Codec<T>::enc((float)(drho + rho * E + L + ne));
-  }
-  const double V[3] = {U[0] - aH * J0[0], U[1] - aH * J0[1], U[2] - aH * J0[2]};
-  for (int bb = 0; bb < 3; ++bb)
-    for (int i = 0; i < kM; ++i) {
-      const int xi[3] = {mx7(i), my7(i), mz7(i)};
-      double l0 = 0.0, ne = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        l0 += xi[a] * (V[a] * B[bb] - B[a] * V[bb]);
-        ne += xi[a] * dB[3 * a + bb];
-      }
-      const double v = b[bb] + 4.0 * l0 - (noneq ? ne / omegaB : 0.0);
-      pop[(long long)mslot(bb, i) * n3 + site] = Codec<T>::enc((float)v);
-    }
-  const double va = sqrt((B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho);
-  const double um = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-  const float sp = (float)fmax(va, um);
-  if (isfinite(sp)) atomicMax(speed_bits, __float_as_uint(sp));
-  else atomicMax(speed_bits, 0x7f800000u);
-}
-
-// ---------------------------------------------------------------------------
-// Moments and decoded populations (FP64 arithmetic from the stored values).
-
-template <class T, bool ODD>
-__device__ __forceinline__ void load_site(const T* __restrict__ pop, int site, const Nbr& nb, long long n3,
-                                          double sf[kQ], double sg[3][kM]) {
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) sf[i] = (double)Codec<T>::dec(pop[src27<ODD>(i, site, nb, n3)]);
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int i = 0; i < kM; ++i) sg[b][i] = (double)Codec<T>::dec(pop[src7<ODD>(b, i, site, nb, n3)]);
-}
-
-struct SiteMoments {
-  double rho, U[3], B[3], J[3], trlam;
-};
-
-__device__ __forceinline__ SiteMoments site_moments(const double sf[kQ], const double sg[3][kM], const StepConsts& k) {
-  SiteMoments m;
-  double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    const double t = w27d(i) * sf[i];
-    drho += t;
-    j[0] += cx27(i) * t;
-    j[1] += cy27(i) * t;
-    j[2] += cz27(i) * t;
-  }
-  m.rho = (double)k.rho0 + drho;
-  for (int a = 0; a < 3; ++a) m.U[a] = j[a] / m.rho;
-  double lam[3][3];
-  for (int b = 0; b < 3; ++b) {
-    m.B[b] = (double)k.Bref[b] + 0.25 * sg[b][0] + 0.125 * (sg[b][1] + sg[b][2] + sg[b][3] + sg[b][4] + sg[b][5] + sg[b][6]);
-    lam[0][b] = 0.125 * (sg[b][1] - sg[b][2]);
-    lam[1][b] = 0.125 * (sg[b][3] - sg[b][4]);
-    lam[2][b] = 0.125 * (sg[b][5] - sg[b][6]);
-  }
-  m.trlam = lam[0][0] + lam[1][1] + lam[2][2];
-  const double gq = 4.0 * (double)k.omegaB;
-  const double* U = m.U;
-  const double* B = m.B;
-  const double A[3] = {lam[1][2] - lam[2][1], lam[2][0] - lam[0][2], lam[0][1] - lam[1][0]};
-  const double uxb[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2], U[0] * B[1] - U[1] * B[0]};
-  const double yv[3] = {-gq * (A[0] - 2.0 * uxb[0]), -gq * (A[1] - 2.0 * uxb[1]), -gq * (A[2] - 2.0 * uxb[2])};
-  const double s = 2.0 * (double)k.alphaH * gq;
-  const double yxb[3] = {yv[1] * B[2] - yv[2] * B[1], yv[2] * B[0] - yv[0] * B[2], yv[0] * B[1] - yv[1] * B[0]};
-  const double yb = yv[0] * B[0] + yv[1] * B[1] + yv[2] * B[2];
-  const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-  for (int a = 0; a < 3; ++a) m.J[a] = (yv[a] - s * yxb[a] + s * s * yb * B[a]) / (1.0 + s * s * b2);
-  return m;
-}
-
-template <class T, bool ODD>
-__global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, double* __restrict__ rho,
-                               double* __restrict__ u, double* __restrict__ B, double* __restrict__ J) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
-  const int site = (z * g.ny + y) * g.nx + x;
-  const Nbr nb = make_nbr(x, y, z, g);
-  double sf[kQ], sg[3][kM];
-  load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
-  const SiteMoments m = site_moments(sf, sg, k);
-  if (rho) rho[site] = m.rho;
-  for (int a = 0; a < 3; ++a) {
-    if (u) u[a * g.n3 + site] = m.U[a];
-    if (B) B[a * g.n3 + site] = m.B[a];
-    if (J) J[a * g.n3 + site] = m.J[a];
-  }
-}
-
-template <class T, bool ODD>
-__global__ void populations_kernel(const T* __restrict__ pop, Grid g, StepConsts k, double* __restrict__ f) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
-  const int site = (z * g.ny + y) * g.nx + x;
-  const Nbr nb = make_nbr(x, y, z, g);
-  double sf[kQ], sg[3][kM];
-  load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
-  const double Br[3] = {(double)k.Bref[0], (double)k.Bref[1], (double)k.Bref[2]};
-  const double br2 = Br[0] * Br[0] + Br[1] * Br[1] + Br[2] * Br[2];
-#pragma unroll 1
-  for (int i = 0; i < kQ; ++i) {
-    const double c2 = cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i);
-    const double cb = cx27(i) * Br[0] + cy27(i) * Br[1] + cz27(i) * Br[2];
-    const double ell = 4.5 * (0.5 * br2 * (c2 - 1.0 / 3.0) - cb * cb);  // rest Lorentz term / w
-    f[(long long)i * g.n3 + site] = w27d(i) * ((double)k.rho0 + ell + sf[i]);
-  }
-  for (int b = 0; b < 3; ++b)
-    for (int i = 0; i < kM; ++i) f[(long long)mslot(b, i) * g.n3 + site] = w7d(i) * (Br[b] + sg[b][i]);
-}
-
-// ---------------------------------------------------------------------------
-// FP64 reduction of the scalar diagnostics: per block, then a fixed-order
-// final sum (deterministic).  Partial layout (kRedVals):
-//   0 sum rho, 1-3 sum rho u, 4-6 sum B, 7 sum |u|^2, 8 sum |B - Bref|^2,
-//   9 sum u.(B - Bref), 10-12 sum u, 13 sum |J|^2, 14 max |u|,
-//   15 sum ((omega_B/C^2) Tr Lambda)^2, 16 non-finite sites.
-template <class T, bool ODD>
-__global__ void reduce_kernel(const T* __restrict__ pop, Grid g, StepConsts k, double* __restrict__ partials) {
-  double acc[kRedVals];
-#pragma unroll
-  for (int v = 0; v < kRedVals; ++v) acc[v] = 0.0;
-  const long long n3 = g.n3;
-  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n3; s += (long long)gridDim.x * blockDim.x) {
-    const int site = (int)s;
-    const int x = site % g.nx, y = (site / g.nx) % g.ny, z = site / (g.nx * g.ny);
-    const Nbr nb = make_nbr(x, y, z, g);
-    double sf[kQ], sg[3][kM];
-    load_site<T, ODD>(pop, site, nb, n3, sf, sg);
-    const SiteMoments m = site_moments(sf, sg, k);
-    const double b[3] = {m.B[0] - k.Bref[0], m.B[1] - k.Bref[1], m.B[2] - k.Bref[2]};
-    const double uu = m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2];
-    const double dv = 4.0 * (double)k.omegaB * m.trlam;
-    const bool ok = isfinite(m.rho + uu + b[0] + b[1] + b[2] + m.J[0] + m.J[1] + m.J[2]);
-    if (!ok) {
-      acc[16] += 1.0;
-      continue;
-    }
-    acc[0] += m.rho;
-    for (int a = 0; a < 3; ++a) {
-      acc[1 + a] += m.rho * m.U[a];
-      acc[4 + a] += m.B[a];
-      acc[10 + a] += m.U[a];
-    }
-    acc[7] += uu;
-    acc[8] += b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-    acc[9] += m.U[0] * b[0] + m.U[1] * b[1] + m.U[2] * b[2];
-    acc[13] += m.J[0] * m.J[0] + m.J[1] * m.J[1] + m.J[2] * m.J[2];
-    acc[14] = fmax(acc[14], sqrt(uu));
-    acc[15] += dv * dv;
-  }
-  // warp, then block
-  __shared__ double sh[32][kRedVals];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < kRedVals; ++v) {
-    double a = acc[v];
-    for (int o = 16; o > 0; o >>= 1) {
-      const double t = __shfl_down_sync(0xffffffffu, a, o);
-      a = (v == 14) ? fmax(a, t) : a + t;
-    }
-    if (lane == 0) sh[warp][v] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x < kRedVals) {
-    const int v = threadIdx.x;
-    double a = sh[0][v];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) a = (v == 14) ? fmax(a, sh[w][v]) : a + sh[w][v];
-    partials[(long long)blockIdx.x * kRedVals + v] = a;
-  }
-}
-
-__global__ void reduce_final_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
-  const int v = threadIdx.x;
-  if (v >= kRedVals) return;
-  double a = partials[v];
-  for (int bk = 1; bk < nblocks; ++bk) a = (v == 14) ? fmax(a, partials[(long long)bk * kRedVals + v]) : a + partials[(long long)bk * kRedVals + v];
-  out[v] = a;
-}
-
-// Block of `threads` threads: x-rows of up to `threads` sites, several
-// rows per block when nx is small.
-dim3 site_block(const Grid& g, int threads = 128) {
-  int bx = g.nx >= threads ? threads : ((g.nx + 31) / 32) * 32;
-  int by = threads / bx;
-  if (by > g.ny) by = g.ny;
-  if (by < 1) by = 1;
-  return dim3(bx, by, 1);
-}
-
-dim3 site_grid(const Grid& g, dim3 b) { return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz); }
 
 template <class T>
 cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s) {
@@ -592,37 +256,6 @@ cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fl
   return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t moments_t(int odd, const void* pop, Grid g, const StepConsts& k, double* rho, double* u, double* B,
-                      double* J, cudaStream_t s) {
-  const dim3 b = site_block(g), gr = site_grid(g, b);
-  if (odd)
-    moments_kernel<T, true><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
-  else
-    moments_kernel<T, false><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
-  return cudaGetLastError();
-}
-
-template <class T>
-cudaError_t populations_t(int odd, const void* pop, Grid g, const StepConsts& k, double* f, cudaStream_t s) {
-  const dim3 b = site_block(g), gr = site_grid(g, b);
-  if (odd)
-    populations_kernel<T, true><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, f);
-  else
-    populations_kernel<T, false><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, f);
-  return cudaGetLastError();
-}
-
-template <class T>
-cudaError_t reduce_t(int odd, const void* pop, Grid g, const StepConsts& k, int nblocks, double* partials,
-                     double* out, cudaStream_t s) {
-  if (odd)
-    reduce_kernel<T, true><<<nblocks, 256, 0, s>>>(static_cast<const T*>(pop), g, k, partials);
-  else
-    reduce_kernel<T, false><<<nblocks, 256, 0, s>>>(static_cast<const T*>(pop), g, k, partials);
-  reduce_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
-  return cudaGetLastError();
-}
 
 }  // namespace
 
@@ -636,70 +269,5 @@ cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConst
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
-                        const double* u, const double* B, const double* gu, const double* gB,
-                        unsigned* speed_bits, cudaStream_t s) {
-  const dim3 b = site_block(g), gr = site_grid(g, b);
-  switch (storage) {
-    case 1: init_kernel<float><<<gr, b, 0, s>>>(static_cast<float*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    case 2: init_kernel<__half><<<gr, b, 0, s>>>(static_cast<__half*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    case 3: init_kernel<__nv_bfloat16><<<gr, b, 0, s>>>(static_cast<__nv_bfloat16*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* rho,
-                           double* u, double* B, double* J, cudaStream_t s) {
-  switch (storage) {
-    case 1: return moments_t<float>(odd, pop, g, k, rho, u, B, J, s);
-    case 2: return moments_t<__half>(odd, pop, g, k, rho, u, B, J, s);
-    case 3: return moments_t<__nv_bfloat16>(odd, pop, g, k, rho, u, B, J, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* f,
-                               cudaStream_t s) {
-  switch (storage) {
-    case 1: return populations_t<float>(odd, pop, g, k, f, s);
-    case 2: return populations_t<__half>(odd, pop, g, k, f, s);
-    case 3: return populations_t<__nv_bfloat16>(odd, pop, g, k, f, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_reduce_partials(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
-                                   double* partials, cudaStream_t s) {
-  if (nblocks < 1) return cudaErrorInvalidValue;
-  switch (storage) {
-    case 1:
-      if (odd) reduce_kernel<float, true><<<nblocks, 256, 0, s>>>(static_cast<const float*>(pop), g, k, partials);
-      else reduce_kernel<float, false><<<nblocks, 256, 0, s>>>(static_cast<const float*>(pop), g, k, partials);
-      break;
-    case 2:
-      if (odd) reduce_kernel<__half, true><<<nblocks, 256, 0, s>>>(static_cast<const __half*>(pop), g, k, partials);
-      else reduce_kernel<__half, false><<<nblocks, 256, 0, s>>>(static_cast<const __half*>(pop), g, k, partials);
-      break;
-    case 3:
-      if (odd) reduce_kernel<__nv_bfloat16, true><<<nblocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(pop), g, k, partials);
-      else reduce_kernel<__nv_bfloat16, false><<<nblocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(pop), g, k, partials);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
-                          double* partials, double* out, cudaStream_t s) {
-  if (nblocks < 1 || nblocks > kRedBlocksMax) return cudaErrorInvalidValue;
-  switch (storage) {
-    case 1: return reduce_t<float>(odd, pop, g, k, nblocks, partials, out, s);
-    case 2: return reduce_t<__half>(odd, pop, g, k, nblocks, partials, out, s);
-    case 3: return reduce_t<__nv_bfloat16>(odd, pop, g, k, nblocks, partials, out, s);
-  }
-  return cudaErrorInvalidValue;
-}
 
 }  // namespace flame
