@@ -170,6 +170,34 @@ flame_status flame_get_state(flame_ctx *ctx, void *d_dst, long long *step, int *
  * Errors: FLAME_ERR_STATE (parity not 0/1, step < 0).  Asynchronous. */
 flame_status flame_set_state(flame_ctx *ctx, const void *d_src, long long step, int parity);
 
+/* Adjoint (vector-Jacobian product) of one flame_step, for gradients of a
+ * loss of a later state (the hand-written reverse of Sec. 3's collision and
+ * streaming; the paper has no adjoint, its equations define the forward map).
+ * d_state: a state blob (flame_state_bytes, as written by flame_get_state)
+ * holding the pre-collision populations at time t with AA parity `parity`.
+ * d_adj_in: [48][N3] FP32, dL/df(t+1) for the physical pre-collision
+ * populations at t+1 in natural slot order (the layout of
+ * flame_populations).  d_adj_out: [48][N3] FP32, receives dL/df(t); must not
+ * alias d_adj_in.  d_ddi: one device double, overwritten with this step's
+ * contribution to dL/d(d_i).  Forward quantities are recomputed from
+ * d_state in FP32; the d_i contribution is summed in FP64.  Asynchronous.
+ * The first call allocates a small per-block workspace.  Errors:
+ * FLAME_ERR_PARAM (null or aliased pointers), FLAME_ERR_STATE (parity),
+ * FLAME_ERR_CUDA. */
+flame_status flame_step_adjoint(flame_ctx *ctx, const void *d_state, int parity, const float *d_adj_in,
+                                float *d_adj_out, double *d_ddi);
+
+/* Adjoint of flame_init for rho = 1 and central-difference gradients (the
+ * d_gradu = d_gradB = NULL case): given d_adj0 = dL/df(0) ([48][N3] FP32,
+ * natural order) and the FP64 fields d_u, d_B it was built from, writes
+ * dL/du ([3][N3], FP64, may be NULL), dL/dB ([3][N3], may be NULL; not both)
+ * and the initial state's contribution to dL/d(d_i) into *d_ddi (device).
+ * Includes the transposed periodic central-difference stencil of J0 = curl B
+ * and of the non-equilibrium parts.  The first call allocates 24 N3 doubles
+ * of workspace.  Asynchronous.  Errors: FLAME_ERR_PARAM, FLAME_ERR_CUDA. */
+flame_status flame_init_adjoint(flame_ctx *ctx, const double *d_u, const double *d_B, const float *d_adj0,
+                                double *d_ubar, double *d_Bbar, double *d_ddi);
+
 /* Largest block count flame_reduce_static accepts; its device scratch holds
  * this many blocks' partial sums (139,264 bytes per device). */
 #define FLAME_STATIC_REDUCE_BLOCKS_MAX 1024

@@ -8,6 +8,8 @@ current obtained from the magnetic non-equilibrium moments.
 - ``Flame``   : ctypes binding of libflame.so (include/flame.h); CUDA only.
 - ``inputs``  : seeded synthetic initial conditions (numpy).
 - ``units``   : lattice-unit parameter mapping and the whistler CFL check.
+- ``adjoint`` : gradients of a band magnetic energy through N steps
+                (FlameBandEnergy autograd Function, sqrt(N) checkpointing).
 - ``build``   : nvcc build of libflame.so for sm_103a.
 """
 from . import inputs, units

@@ -1,0 +1,554 @@
+// adjoint.cu -- hand-written vector-Jacobian products of the FLAME step and
+// of the initialisation, for gradients of a loss of the final state with
+// respect to the initial fields and the Hall length d_i.
+//
+// Step.  With lambda_{t+1} = dL/df(t+1) (pre-collision populations, natural
+// slot order), streaming f(x, q, t+1) = f*(x - c_q, q, t) gives
+// dL/df*(x, q) = lambda_{t+1}(x + c_q, q), and the per-site collision's
+// transpose Jacobian maps it to lambda_t.  The forward quantities of the
+// site (rho, U, Pi, B, Lambda, J, V, D) are recomputed from the state at t.
+// Reverse sweep per site (physical populations f, g; gamma = omega_B/C^2,
+// s = 2 gamma alpha_H, M = I + s [. x B]):
+//   g*  = (1-wB) g + wB g^eq(B, V):   gbar = (1-wB) gbar*; mu = wB W_i gbar*;
+//        Bbar += m0 + 4 Q^T V - 4 Q V, Vbar = 4 Q B - 4 Q^T B with
+//        m0_b = sum_i mu_bi, Q_ab = sum_i mu_bi xi_ia;
+//   V = U - alpha J:  Ubar += Vbar, Jbar = -alpha Vbar, abar -= Vbar.J;
+//   J = M^-1 y:       lJ = M^-T Jbar (same closed form with s -> -s),
+//        ybar = lJ, sbar = -lJ.(J x B), Bbar -= s lJ x J;
+//   s = 2 gamma alpha: abar += 2 gamma sbar;
+//   y = -gamma (A - 2 U x B): Abar = -gamma ybar, Ubar += 2 gamma B x ybar,
+//        Bbar += 2 gamma ybar x U; Lambdabar_ab = eps_cab Abar_c;
+//   f* = rho prod psi(U) + Lorentz(B) + P(D, U), D = (1-w) dev(Pi - rho U U - M(B)):
+//        contractions of fbar* with the products of 1-D functions and their
+//        U derivatives give rhobar, Ubar, Dbar; Lorentz gives
+//        Bbar += 4.5 (tr H B - 2 H B), H = sum_i fbar*_i w_i H2_i;
+//        Dbar -> Sbar -> (Pibar, rhobar, Ubar, Bbar);
+//   U = j/rho: jbar = Ubar/rho, rhobar -= Ubar.U/rho;
+//   moments: fbar_i = rhobar + jbar.c_i + Pibar : c_i c_i,
+//            gbar_bi += Bbar_b + sum_a xi_ia Lambdabar_ab.
+#include "aa.cuh"
+
+namespace flame {
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+// 1-D functions of the undivided equilibrium and inverse-moment maps, and
+// their derivatives in u, at velocity component c (index p = c + 1).
+struct Axis {
+  float psi[3], dpsi[3], F0[3], F1[3], dF0[3];
+  __device__ __forceinline__ explicit Axis(float u) {
+    const float uu = u * u;
+    psi[1] = 2.f / 3.f - uu;
+    dpsi[1] = -2.f * u;
+    F0[1] = 1.f - uu;
+    F1[1] = -2.f * u;
+    dF0[1] = -2.f * u;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float c = h == 0 ? -1.f : 1.f;
+      const int p = h == 0 ? 0 : 2;
+      psi[p] = 0.5f * (1.f / 3.f + uu + c * u);
+      dpsi[p] = u + 0.5f * c;
+      F0[p] = 0.5f * (uu + c * u);
+      F1[p] = u + 0.5f * c;
+      dF0[p] = u + 0.5f * c;
+    }
+  }
+};
+__device__ __forceinline__ float F2(int p) { return p == 1 ? -1.f : 0.5f; }
+__device__ __forceinline__ float dF1(int p) { return p == 1 ? -2.f : 1.f; }
+
+__device__ __forceinline__ void block_sum_to(double v, double* out) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double a = 0.0;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    for (int w = 0; w < nw; ++w) a += sh[w];
+    *out = a;
+  }
+}
+
+template <class T, bool ODD>
+__global__ void __launch_bounds__(kAdjThreads)
+    adjoint_step_kernel(Slots<T> P, Grid g, StepConsts k, const float* __restrict__ lam_in,
+                        float* __restrict__ lam_out, double* __restrict__ partials) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool live = x < g.nx && y < g.ny;
+  double abar_site = 0.0;
+  if (live) {
+    const int site = (z * g.ny + y) * g.nx + x;
+    const Nbr nb = make_nbr(x, y, z, g);
+    const long long n3 = g.n3;
+
+    // ---- forward recompute (deviation variables, as in the step kernel)
+    float sf[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int slot = ODD ? opp27(i) : i;
+      sf[i] = Codec<T>::dec(P.p[slot][site + src_off<ODD>(nb, cx27(i), cy27(i), cz27(i))]);
+    }
+    float sg[3][kM];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int i = 0; i < kM; ++i)
+        sg[b][i] = Codec<T>::dec(P.p[mslot(b, ODD ? opp7(i) : i)][site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i))]);
+    float drho = 0.f, jv[3] = {0.f, 0.f, 0.f}, pv[3][3] = {{0.f}};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const float t = (float)w27x216(i) * sf[i];
+      const int c[3] = {cx27(i), cy27(i), cz27(i)};
+      drho += t;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (c[a] != 0) jv[a] += c[a] > 0 ? t : -t;
+#pragma unroll
+        for (int b = a; b < 3; ++b)
+          if (c[a] * c[b] != 0) pv[a][b] += c[a] * c[b] > 0 ? t : -t;
+      }
+    }
+    drho /= 216.f;
+    const float rho = k.rho0 + drho;
+    const float U[3] = {jv[0] / (216.f * rho), jv[1] / (216.f * rho), jv[2] / (216.f * rho)};
+    float dB[3], lam[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      dB[b] = 0.25f * sg[b][0] + 0.125f * (sg[b][1] + sg[b][2] + sg[b][3] + sg[b][4] + sg[b][5] + sg[b][6]);
+      lam[0][b] = 0.125f * (sg[b][1] - sg[b][2]);
+      lam[1][b] = 0.125f * (sg[b][3] - sg[b][4]);
+      lam[2][b] = 0.125f * (sg[b][5] - sg[b][6]);
+    }
+    const float B[3] = {k.Bref[0] + dB[0], k.Bref[1] + dB[1], k.Bref[2] + dB[2]};
+    const float gam = 4.f * k.omegaB, al = k.alphaH;
+    const float Av[3] = {lam[1][2] - lam[2][1], lam[2][0] - lam[0][2], lam[0][1] - lam[1][0]};
+    float yv[3];
+    {
+      const float uxb[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2], U[0] * B[1] - U[1] * B[0]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) yv[a] = -gam * (Av[a] - 2.f * uxb[a]);
+    }
+    const float s = 2.f * gam * al;
+    const float b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const float iden = 1.f / (1.f + s * s * b2);
+    float J[3], V[3];
+    {
+      const float yxb[3] = {yv[1] * B[2] - yv[2] * B[1], yv[2] * B[0] - yv[0] * B[2], yv[0] * B[1] - yv[1] * B[0]};
+      const float yb = yv[0] * B[0] + yv[1] * B[1] + yv[2] * B[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        J[a] = (yv[a] - s * yxb[a] + s * s * yb * B[a]) * iden;
+        V[a] = U[a] - al * J[a];
+      }
+    }
+    // D = (1 - w) dev(Pi - rho U U - M(B)); in deviations dev(Pi~ - rho U U + N)
+    float D[3][3];
+    {
+      const float Br[3] = {k.Bref[0], k.Bref[1], k.Bref[2]};
+      float S[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) {
+          const float N = Br[a] * dB[b] + dB[a] * Br[b] + dB[a] * dB[b];
+          S[a][b] = pv[a][b] / 216.f - rho * U[a] * U[b] + N;
+        }
+      const float r = 1.f - k.omega;
+      const float tr3 = (S[0][0] + S[1][1] + S[2][2]) / 3.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) D[a][b] = r * (a == b ? S[a][b] - tr3 : S[a][b]);
+    }
+
+    // ---- gather dL/df* (streaming transpose: from x + c_q)
+    float lf[kQ], lg[3][kM];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) lf[i] = lam_in[(long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int i = 0; i < kM; ++i)
+        lg[b][i] = lam_in[(long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))];
+
+    // ---- magnetic collision
+    const float omB = k.omegaB;
+    float Bb[3], Vb[3], Q[3][3];  // Q[a][b] = sum_i mu_bi xi_ia
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float m0 = 0.25f * lg[b][0];
+#pragma unroll
+      for (int i = 1; i < kM; ++i) m0 += 0.125f * lg[b][i];
+      Bb[b] = omB * m0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Q[a][b] = omB * 0.125f * (lg[b][2 * a + 1] - lg[b][2 * a + 2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float qtv = 0.f, qv = 0.f, qb = 0.f, qtb = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        qtv += Q[a][c] * V[a];
+        qv += Q[c][a] * V[a];
+        qb += Q[c][a] * B[a];
+        qtb += Q[a][c] * B[a];
+      }
+      Bb[c] += 4.f * (qtv - qv);
+      Vb[c] = 4.f * (qb - qtb);
+    }
+    float Ub[3] = {Vb[0], Vb[1], Vb[2]};
+    float Jb[3] = {-al * Vb[0], -al * Vb[1], -al * Vb[2]};
+    float abar = -(Vb[0] * J[0] + Vb[1] * J[1] + Vb[2] * J[2]);
+    // J = M^-1 y
+    float lJ[3];
+    {
+      const float jxb[3] = {Jb[1] * B[2] - Jb[2] * B[1], Jb[2] * B[0] - Jb[0] * B[2], Jb[0] * B[1] - Jb[1] * B[0]};
+      const float jb = Jb[0] * B[0] + Jb[1] * B[1] + Jb[2] * B[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) lJ[a] = (Jb[a] + s * jxb[a] + s * s * jb * B[a]) * iden;
+    }
+    {
+      const float JxB[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
+      const float sbar = -(lJ[0] * JxB[0] + lJ[1] * JxB[1] + lJ[2] * JxB[2]);
+      abar += 2.f * gam * sbar;
+      const float lxj[3] = {lJ[1] * J[2] - lJ[2] * J[1], lJ[2] * J[0] - lJ[0] * J[2], lJ[0] * J[1] - lJ[1] * J[0]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Bb[a] -= s * lxj[a];
+    }
+    // y = -gamma (A - 2 U x B)
+    float Lb[3][3];
+    {
+      const float* yb = lJ;
+      const float bxy[3] = {B[1] * yb[2] - B[2] * yb[1], B[2] * yb[0] - B[0] * yb[2], B[0] * yb[1] - B[1] * yb[0]};
+      const float yxu[3] = {yb[1] * U[2] - yb[2] * U[1], yb[2] * U[0] - yb[0] * U[2], yb[0] * U[1] - yb[1] * U[0]};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Ub[a] += 2.f * gam * bxy[a];
+        Bb[a] += 2.f * gam * yxu[a];
+      }
+      const float Ab[3] = {-gam * yb[0], -gam * yb[1], -gam * yb[2]};
+      Lb[0][0] = Lb[1][1] = Lb[2][2] = 0.f;
+      Lb[1][2] = Ab[0];
+      Lb[2][1] = -Ab[0];
+      Lb[2][0] = Ab[1];
+      Lb[0][2] = -Ab[1];
+      Lb[0][1] = Ab[2];
+      Lb[1][0] = -Ab[2];
+    }
+
+    // ---- fluid collision: contractions of fbar* = lf
+    const Axis ax(U[0]), ay(U[1]), az(U[2]);
+    const float Dxx = D[0][0], Dyy = D[1][1], Dzz = D[2][2], Dxy = D[0][1], Dxz = D[0][2], Dyz = D[1][2];
+    float rb = 0.f, Ueq[3] = {0.f, 0.f, 0.f}, UP[3] = {0.f, 0.f, 0.f};
+    float Dbxx = 0.f, Dbyy = 0.f, Dbzz = 0.f, Dbxy = 0.f, Dbxz = 0.f, Dbyz = 0.f;
+    float r0 = 0.f, R[3][3] = {{0.f}};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int px = cx27(i) + 1, py = cy27(i) + 1, pz = cz27(i) + 1;
+      const float t = lf[i];
+      const float pxy = ax.psi[px] * ay.psi[py];
+      rb += t * pxy * az.psi[pz];
+      Ueq[0] += t * ax.dpsi[px] * ay.psi[py] * az.psi[pz];
+      Ueq[1] += t * ax.psi[px] * ay.dpsi[py] * az.psi[pz];
+      Ueq[2] += t * pxy * az.dpsi[pz];
+      const float f0x = ax.F0[px], f0y = ay.F0[py], f0z = az.F0[pz];
+      const float f1x = ax.F1[px], f1y = ay.F1[py], f1z = az.F1[pz];
+      const float f2x = F2(px), f2y = F2(py), f2z = F2(pz);
+      Dbxx += t * f2x * f0y * f0z;
+      Dbyy += t * f0x * f2y * f0z;
+      Dbzz += t * f0x * f0y * f2z;
+      Dbxy += t * f1x * f1y * f0z;
+      Dbxz += t * f1x * f0y * f1z;
+      Dbyz += t * f0x * f1y * f1z;
+      // derivative of P in U_a: only the a-axis factor is differentiated
+      UP[0] += t * (ax.dF0[px] * (Dyy * f2y * f0z + Dzz * f0y * f2z + Dyz * f1y * f1z) +
+                    dF1(px) * (Dxy * f1y * f0z + Dxz * f0y * f1z));
+      UP[1] += t * (ay.dF0[py] * (Dxx * f2x * f0z + Dzz * f0x * f2z + Dxz * f1x * f1z) +
+                    dF1(py) * (Dxy * f1x * f0z + Dyz * f0x * f1z));
+      UP[2] += t * (az.dF0[pz] * (Dxx * f2x * f0y + Dyy * f0x * f2y + Dxy * f1x * f1y) +
+                    dF1(pz) * (Dxz * f1x * f0y + Dyz * f0x * f1y));
+      const float wt = (float)w27d(i) * t;
+      const int c[3] = {px - 1, py - 1, pz - 1};
+      r0 += wt;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b)
+          if (c[a] * c[b] != 0) R[a][b] += c[a] * c[b] > 0 ? wt : -wt;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Ub[a] += rho * Ueq[a] + UP[a];
+    // Lorentz: H = R - r0 I / 3
+    {
+      const float H[3][3] = {{R[0][0] - r0 / 3.f, R[0][1], R[0][2]},
+                             {R[0][1], R[1][1] - r0 / 3.f, R[1][2]},
+                             {R[0][2], R[1][2], R[2][2] - r0 / 3.f}};
+      const float trH = H[0][0] + H[1][1] + H[2][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Bb[a] += 4.5f * (trH * B[a] - 2.f * (H[a][0] * B[0] + H[a][1] * B[1] + H[a][2] * B[2]));
+    }
+    // D -> S -> (Pi, rho, U, B)
+    const float r = 1.f - k.omega;
+    const float trD3 = (Dbxx + Dbyy + Dbzz) / 3.f;
+    const float Sb[3][3] = {{r * (Dbxx - trD3), r * Dbxy, r * Dbxz},
+                            {r * Dbxy, r * (Dbyy - trD3), r * Dbyz},
+                            {r * Dbxz, r * Dbyz, r * (Dbzz - trD3)}};
+    {
+      const float trS = Sb[0][0] + Sb[1][1] + Sb[2][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        rb -= Sb[a][a] * U[a] * U[a];
+        Ub[a] -= 2.f * rho * Sb[a][a] * U[a];
+        Bb[a] += -trS * B[a] + 2.f * Sb[a][a] * B[a];
+      }
+      const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const int a = pa[p], b = pb[p];
+        rb -= Sb[a][b] * U[a] * U[b];
+        Ub[a] -= rho * Sb[a][b] * U[b];
+        Ub[b] -= rho * Sb[a][b] * U[a];
+        Bb[a] += Sb[a][b] * B[b];
+        Bb[b] += Sb[a][b] * B[a];
+      }
+    }
+    // U = j / rho
+    const float jb[3] = {Ub[0] / rho, Ub[1] / rho, Ub[2] / rho};
+    rb -= (Ub[0] * U[0] + Ub[1] * U[1] + Ub[2] * U[2]) / rho;
+
+    // ---- moments -> populations
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int c[3] = {cx27(i), cy27(i), cz27(i)};
+      float v = rb;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (c[a] != 0) v += c[a] > 0 ? jb[a] : -jb[a];
+#pragma unroll
+        for (int b = a; b < 3; ++b)
+          if (c[a] * c[b] != 0) v += c[a] * c[b] > 0 ? Sb[a][b] : -Sb[a][b];
+      }
+      lam_out[(long long)i * n3 + site] = v;
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int i = 0; i < kM; ++i) {
+        float v = (1.f - omB) * lg[b][i] + Bb[b];
+        if (i > 0) {
+          const int a = (i - 1) >> 1;
+          v += (i & 1) ? Lb[a][b] : -Lb[a][b];
+        }
+        lam_out[(long long)mslot(b, i) * n3 + site] = v;
+      }
+    abar_site = (double)abar;
+  }
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  block_sum_to(abar_site, partials + blk);
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation adjoint (FP64), local part: per site the contributions to
+// u_bar and B_bar that do not go through a gradient, and the adjoints of the
+// central-difference gradients (d_a u_b, d_a B_b at [3a+b]).
+__global__ void init_adjoint_local_kernel(Grid g, StepConsts k, const double* __restrict__ u,
+                                          const double* __restrict__ Bf, const float* __restrict__ lam,
+                                          double* __restrict__ ubl, double* __restrict__ Bbl,
+                                          double* __restrict__ dub, double* __restrict__ dBb,
+                                          double* __restrict__ partials) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  double abar = 0.0;
+  if (x < g.nx && y < g.ny) {
+    const long long n3 = g.n3;
+    const long long site = ((long long)z * g.ny + y) * g.nx + x;
+    const double U[3] = {u[site], u[n3 + site], u[2 * n3 + site]};
+    const double B[3] = {Bf[site], Bf[n3 + site], Bf[2 * n3 + site]};
+    // central-difference gradient of B for J0 = curl B
+    const int xp = x + 1 == g.nx ? 0 : x + 1, xm = x == 0 ? g.nx - 1 : x - 1;
+    const int yp = y + 1 == g.ny ? 0 : y + 1, ym = y == 0 ? g.ny - 1 : y - 1;
+    const int zp = z + 1 == g.nz ? 0 : z + 1, zm = z == 0 ? g.nz - 1 : z - 1;
+    auto at = [&](int xx, int yy, int zz) { return ((long long)zz * g.ny + yy) * g.nx + xx; };
+    double dB[3][3];
+    for (int b = 0; b < 3; ++b) {
+      const double* F = Bf + b * n3;
+      dB[0][b] = 0.5 * (F[at(xp, y, z)] - F[at(xm, y, z)]);
+      dB[1][b] = 0.5 * (F[at(x, yp, z)] - F[at(x, ym, z)]);
+      dB[2][b] = 0.5 * (F[at(x, y, zp)] - F[at(x, y, zm)]);
+    }
+    const double al = (double)k.alphaH, omB = (double)k.omegaB, om = (double)k.omega;
+    const double J0[3] = {dB[1][2] - dB[2][1], dB[2][0] - dB[0][2], dB[0][1] - dB[1][0]};
+    const double V[3] = {U[0] - al * J0[0], U[1] - al * J0[1], U[2] - al * J0[2]};
+    double lf[kQ], lg[3][kM];
+    for (int i = 0; i < kQ; ++i) lf[i] = (double)lam[(long long)i * n3 + site];
+    for (int b = 0; b < 3; ++b)
+      for (int i = 0; i < kM; ++i) lg[b][i] = (double)lam[(long long)mslot(b, i) * n3 + site];
+    // H = sum_i lf w H2; Lorentz part of B_bar; equilibrium part of u_bar
+    double r0 = 0.0, R[3][3] = {{0.0}}, Ub[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < kQ; ++i) {
+      const int c[3] = {cx27(i), cy27(i), cz27(i)};
+      const double wt = w27d(i) * lf[i];
+      r0 += wt;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) R[a][b] += wt * c[a] * c[b];
+      double ps[3], dps[3];
+      for (int a = 0; a < 3; ++a) {
+        const double uu = U[a] * U[a];
+        ps[a] = c[a] == 0 ? 2.0 / 3.0 - uu : 0.5 * (1.0 / 3.0 + uu + c[a] * U[a]);
+        dps[a] = c[a] == 0 ? -2.0 * U[a] : U[a] + 0.5 * c[a];
+      }
+      Ub[0] += lf[i] * dps[0] * ps[1] * ps[2];
+      Ub[1] += lf[i] * ps[0] * dps[1] * ps[2];
+      Ub[2] += lf[i] * ps[0] * ps[1] * dps[2];
+    }
+    double H[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) H[a][b] = R[a][b] - (a == b ? r0 / 3.0 : 0.0);
+    const double trH = H[0][0] + H[1][1] + H[2][2];
+    double Bb[3];
+    for (int a = 0; a < 3; ++a) Bb[a] = 4.5 * (trH * B[a] - 2.0 * (H[a][0] * B[0] + H[a][1] * B[1] + H[a][2] * B[2]));
+    // Hall equilibrium: mu = W lg, m0, Q[a][b] = sum_i mu_bi xi_ia
+    double Q[3][3], Vb[3];
+    for (int b = 0; b < 3; ++b) {
+      double m0 = 0.25 * lg[b][0];
+      for (int i = 1; i < kM; ++i) m0 += 0.125 * lg[b][i];
+      Bb[b] += m0;
+      for (int a = 0; a < 3; ++a) Q[a][b] = 0.125 * (lg[b][2 * a + 1] - lg[b][2 * a + 2]);
+    }
+    for (int c = 0; c < 3; ++c) {
+      double qtv = 0.0, qv = 0.0, qb = 0.0, qtb = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        qtv += Q[a][c] * V[a];
+        qv += Q[c][a] * V[a];
+        qb += Q[c][a] * B[a];
+        qtb += Q[a][c] * B[a];
+      }
+      Bb[c] += 4.0 * (qtv - qv);
+      Vb[c] = 4.0 * (qb - qtb);
+    }
+    for (int a = 0; a < 3; ++a) Ub[a] += Vb[a];
+    const double J0b[3] = {-al * Vb[0], -al * Vb[1], -al * Vb[2]};
+    abar = -(Vb[0] * J0[0] + Vb[1] * J0[1] + Vb[2] * J0[2]);
+    double db[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) db[a][b] = -Q[a][b] / omB;
+    db[1][2] += J0b[0];
+    db[2][1] -= J0b[0];
+    db[2][0] += J0b[1];
+    db[0][2] -= J0b[1];
+    db[0][1] += J0b[2];
+    db[1][0] -= J0b[2];
+    for (int a = 0; a < 3; ++a) {
+      ubl[a * n3 + site] = Ub[a];
+      Bbl[a * n3 + site] = Bb[a];
+      for (int b = 0; b < 3; ++b) {
+        dBb[(3 * a + b) * n3 + site] = db[a][b];
+        dub[(3 * a + b) * n3 + site] = -(3.0 / om) * H[a][b];  // rho = 1 initial density
+      }
+    }
+  }
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  block_sum_to(abar, partials + blk);
+}
+
+// Transpose of the periodic central difference: F_bar(y) += 1/2 (G(y - e_a) - G(y + e_a)).
+__global__ void init_adjoint_stencil_kernel(Grid g, const double* __restrict__ ubl, const double* __restrict__ Bbl,
+                                            const double* __restrict__ dub, const double* __restrict__ dBb,
+                                            double* __restrict__ ubar, double* __restrict__ Bbar) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const long long n3 = g.n3;
+  const long long site = ((long long)z * g.ny + y) * g.nx + x;
+  const int xp = x + 1 == g.nx ? 0 : x + 1, xm = x == 0 ? g.nx - 1 : x - 1;
+  const int yp = y + 1 == g.ny ? 0 : y + 1, ym = y == 0 ? g.ny - 1 : y - 1;
+  const int zp = z + 1 == g.nz ? 0 : z + 1, zm = z == 0 ? g.nz - 1 : z - 1;
+  const long long m[3] = {((long long)z * g.ny + y) * g.nx + xm, ((long long)z * g.ny + ym) * g.nx + x,
+                          ((long long)zm * g.ny + y) * g.nx + x};
+  const long long p[3] = {((long long)z * g.ny + y) * g.nx + xp, ((long long)z * g.ny + yp) * g.nx + x,
+                          ((long long)zp * g.ny + y) * g.nx + x};
+  for (int b = 0; b < 3; ++b) {
+    double vb = Bbl[b * n3 + site], vu = ubl[b * n3 + site];
+    for (int a = 0; a < 3; ++a) {
+      const double* G = dBb + (3 * a + b) * n3;
+      const double* Gu = dub + (3 * a + b) * n3;
+      vb += 0.5 * (G[m[a]] - G[p[a]]);
+      vu += 0.5 * (Gu[m[a]] - Gu[p[a]]);
+    }
+    if (Bbar) Bbar[b * n3 + site] = vb;
+    if (ubar) ubar[b * n3 + site] = vu;
+  }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partials, long long n, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) a += partials[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+template <class T>
+cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, const float* lin, float* lout,
+                      double* partials, long long nblk, double* ddi, cudaStream_t s) {
+  const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
+  Slots<T> P;
+  for (int q = 0; q < kPop; ++q) P.p[q] = const_cast<T*>(static_cast<const T*>(pop)) + (size_t)q * (size_t)g.n3;
+  if (odd)
+    adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, lin, lout, partials);
+  else
+    adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, lin, lout, partials);
+  sum_partials_kernel<<<1, 256, 0, s>>>(partials, nblk, ddi);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+long long adjoint_partials_needed(Grid g) {
+  const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
+  const dim3 bi = site_block(g, 128), gi = site_grid(g, bi);
+  const long long a = (long long)gr.x * gr.y * gr.z, c = (long long)gi.x * gi.y * gi.z;
+  return a > c ? a : c;
+}
+
+cudaError_t launch_step_adjoint(int storage, int odd, const void* pop, Grid g, const StepConsts& k, const float* lin,
+                                float* lout, double* partials, double* ddi, cudaStream_t s) {
+  const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
+  const long long nblk = (long long)gr.x * gr.y * gr.z;
+  switch (storage) {
+    case 1: return adjoint_t<float>(odd, pop, g, k, lin, lout, partials, nblk, ddi, s);
+    case 2: return adjoint_t<__half>(odd, pop, g, k, lin, lout, partials, nblk, ddi, s);
+    case 3: return adjoint_t<__nv_bfloat16>(odd, pop, g, k, lin, lout, partials, nblk, ddi, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init_adjoint(Grid g, const StepConsts& k, const double* u, const double* B, const float* lam,
+                                double* ws, double* partials, double* ubar, double* Bbar, double* ddi,
+                                cudaStream_t s) {
+  const dim3 b = site_block(g, 128), gr = site_grid(g, b);
+  const long long n3 = g.n3;
+  double* ubl = ws;
+  double* Bbl = ws + 3 * n3;
+  double* dub = ws + 6 * n3;
+  double* dBb = ws + 15 * n3;
+  init_adjoint_local_kernel<<<gr, b, 0, s>>>(g, k, u, B, lam, ubl, Bbl, dub, dBb, partials);
+  init_adjoint_stencil_kernel<<<gr, b, 0, s>>>(g, ubl, Bbl, dub, dBb, ubar, Bbar);
+  sum_partials_kernel<<<1, 256, 0, s>>>(partials, (long long)gr.x * gr.y * gr.z, ddi);
+  return cudaGetLastError();
+}
+
+}  // namespace flame

@@ -32,6 +32,8 @@ struct flame_ctx {
   int nshell_cap;
   cufftHandle plan;
   bool has_plan;
+  double* d_adj_partials;  // adjoint_partials_needed doubles
+  double* d_adj_ws;        // 24 * N3 doubles (initialisation adjoint)
   flame::StepConsts k;
   flame::Grid g;
 };
@@ -414,6 +416,47 @@ flame_status flame_set_state(flame_ctx* c, const void* d_src, long long step, in
   return FLAME_OK;
 }
 
+flame_status flame_step_adjoint(flame_ctx* c, const void* d_state, int parity, const float* d_adj_in,
+                                float* d_adj_out, double* d_ddi) {
+  if (!c || !d_state || !d_adj_in || !d_adj_out || !d_ddi) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  if (parity != 0 && parity != 1) return FLAME_ERR_STATE;
+  if (d_adj_in == d_adj_out) return FLAME_ERR_PARAM;
+  cudaError_t e;
+  if (!c->d_adj_partials) {
+    e = cudaMalloc(&c->d_adj_partials, sizeof(double) * (size_t)flame::adjoint_partials_needed(c->g));
+    if (e != cudaSuccess) {
+      c->d_adj_partials = nullptr;
+      return cuda_fail(c, e);
+    }
+  }
+  return cuda_fail(c, flame::launch_step_adjoint(c->p.storage, parity, d_state, c->g, c->k, d_adj_in, d_adj_out,
+                                                 c->d_adj_partials, d_ddi, c->stream));
+}
+
+flame_status flame_init_adjoint(flame_ctx* c, const double* d_u, const double* d_B, const float* d_adj0,
+                                double* d_ubar, double* d_Bbar, double* d_ddi) {
+  if (!c || !d_u || !d_B || !d_adj0 || !d_ddi || (!d_ubar && !d_Bbar)) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  cudaError_t e;
+  if (!c->d_adj_partials) {
+    e = cudaMalloc(&c->d_adj_partials, sizeof(double) * (size_t)flame::adjoint_partials_needed(c->g));
+    if (e != cudaSuccess) {
+      c->d_adj_partials = nullptr;
+      return cuda_fail(c, e);
+    }
+  }
+  if (!c->d_adj_ws) {
+    e = cudaMalloc(&c->d_adj_ws, sizeof(double) * 24 * (size_t)c->g.n3);
+    if (e != cudaSuccess) {
+      c->d_adj_ws = nullptr;
+      return cuda_fail(c, e);
+    }
+  }
+  return cuda_fail(c, flame::launch_init_adjoint(c->g, c->k, d_u, d_B, d_adj0, c->d_adj_ws, c->d_adj_partials,
+                                                 d_ubar, d_Bbar, d_ddi, c->stream));
+}
+
 void flame_destroy(flame_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
@@ -423,6 +466,8 @@ void flame_destroy(flame_ctx* c) {
   cudaFree(c->d_fields);
   cudaFree(c->d_spec);
   cudaFree(c->d_shells);
+  cudaFree(c->d_adj_partials);
+  cudaFree(c->d_adj_ws);
   delete c;
 }
 

@@ -64,6 +64,18 @@ struct CtxView {
   double Bref[3];
 };
 
+// Adjoint kernels (adjoint.cu).  The step adjoint reads the forward state at
+// time t (AA parity `odd`), lambda_{t+1} and writes lambda_t (FP32, natural
+// slot order [48][N3]); both write one partial d(loss)/d(d_i) per block into
+// `partials` (adjoint_partials_needed(g) doubles) and its sum into *ddi.
+long long adjoint_partials_needed(Grid g);
+cudaError_t launch_step_adjoint(int storage, int odd, const void* pop, Grid g, const StepConsts& k, const float* lin,
+                                float* lout, double* partials, double* ddi, cudaStream_t s);
+// ws: 24 * N3 doubles of workspace.
+cudaError_t launch_init_adjoint(Grid g, const StepConsts& k, const double* u, const double* B, const float* lam,
+                                double* ws, double* partials, double* ubar, double* Bbar, double* ddi,
+                                cudaStream_t s);
+
 cudaError_t launch_shell_bin(const void* spec /* cufftDoubleComplex */, Grid g, int nshell, int zero_mean,
                              double* shells, cudaStream_t s);
 

@@ -84,6 +84,8 @@ def _lib():
             "flame_status_string": (ctypes.c_char_p, [i]),
             "flame_lattice": (i, [P(i), P(i)]),
             "flame_reduce_static": (i, [vp, i, vp]),
+            "flame_step_adjoint": (i, [vp, vp, i, vp, vp, vp]),
+            "flame_init_adjoint": (i, [vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
