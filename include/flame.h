@@ -70,6 +70,9 @@ typedef struct {
     int check_every;  /* > 0: flame_step synchronises and checks the non-finite flag
                          every check_every steps; 0: only flame_sync checks               */
     int strict_cfl;   /* 1: flame_init fails with FLAME_ERR_CFL if pi d_i max(V_A,|u|) > 1 */
+    int graph_steps;  /* 0: one kernel launch per step; even G > 0: flame_step replays a
+                         captured CUDA graph of G steps for each whole chunk of G steps
+                         (removes launch overhead on small lattices)                    */
 } flame_params;
 
 typedef struct {
@@ -98,6 +101,7 @@ enum {
 typedef struct flame_ctx flame_ctx;
 
 /* Bytes of the population state: 48 * N3 * (4 for FP32, 2 for FP16/BF16).
+ * graph_steps must be 0 or a positive even number. 
  * Returns 0 for invalid parameters. */
 size_t flame_state_bytes(const flame_params *p);
 
@@ -122,7 +126,9 @@ flame_status flame_create(flame_ctx **out, const flame_params *p, void *d_state,
 flame_status flame_init(flame_ctx *ctx, const double *d_rho, const double *d_u, const double *d_B,
                         const double *d_gradu, const double *d_gradB);
 
-/* Advance n >= 0 time steps, one fused kernel launch per step: moments
+/* Advance n >= 0 time steps, one fused kernel launch per step (or, with
+ * graph_steps = G, graph replays of G launches; the graph is captured on the
+ * first use for each starting parity, on a private stream): moments
  * (eqs. LB_moments2, mag_field_LB), current from the 3x3 Hall system (eqs.
  * LB_density_current, soe_current_density), central-moment fluid collision
  * (eqs. cm_collision_step, collision_matrix), Hall-equilibrium BGK magnetic
@@ -141,6 +147,14 @@ flame_status flame_info(flame_ctx *ctx, flame_info_t *out);
  * rho [N3], u [3][N3], B [3][N3], J [3][N3] (J from the Hall linear system,
  * as in the step).  Any pointer may be NULL.  Asynchronous. */
 flame_status flame_moments(flame_ctx *ctx, double *d_rho, double *d_u, double *d_B, double *d_J);
+
+/* Moments at a list of sites, for time series such as the velocity at a
+ * fixed point that Sec. 4.1-4.2 follow: d_sites [nsites] linear site indices
+ * (z*ny + y)*nx + x (device), d_out [nsites][10] FP64 (device): rho, u[3],
+ * B[3], J[3] of the current pre-collision populations.  An index outside the
+ * lattice yields NaNs for that entry.  Asynchronous.  Errors:
+ * FLAME_ERR_PARAM, FLAME_ERR_STATE (no flame_init). */
+flame_status flame_probe(flame_ctx *ctx, int nsites, const long long *d_sites, double *d_out);
 
 /* The current pre-collision populations decoded to FP64 in natural order,
  * d_f [48][N3] with the slot numbering above, whatever the AA parity.

@@ -32,6 +32,8 @@ struct flame_ctx {
   int nshell_cap;
   cufftHandle plan;
   bool has_plan;
+  cudaGraphExec_t graph[2];  // graph_steps launches starting at parity 0 / 1
+  bool has_graph[2];
   double* d_adj_partials;  // adjoint_partials_needed doubles
   double* d_adj_ws;        // 24 * N3 doubles (initialisation adjoint)
   flame::StepConsts k;
@@ -56,6 +58,7 @@ flame_status check_params(const flame_params* p) {
     if (!std::isfinite(p->B_ref[a])) return FLAME_ERR_PARAM;
   if (elem_bytes(p->storage) == 0) return FLAME_ERR_PARAM;
   if (p->check_every < 0) return FLAME_ERR_PARAM;
+  if (p->graph_steps < 0 || (p->graph_steps & 1)) return FLAME_ERR_PARAM;
   return FLAME_OK;
 }
 
@@ -229,11 +232,48 @@ flame_status flame_init(flame_ctx* c, const double* d_rho, const double* d_u, co
   return FLAME_OK;
 }
 
+// Capture graph_steps step launches starting at `parity` into c->graph[parity].
+static cudaError_t capture_graph(flame_ctx* c, int parity) {
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < c->p.graph_steps && le == cudaSuccess; ++i)
+      le = flame::launch_step(c->p.storage, parity ^ (i & 1), c->state, c->g, c->k, c->d_flags, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[parity], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e == cudaSuccess) c->has_graph[parity] = true;
+  return e;
+}
+
 flame_status flame_step(flame_ctx* c, int n) {
   flame_status st = usable(c);
   if (st != FLAME_OK) return st;
   if (n < 0) return FLAME_ERR_PARAM;
   if (!c->initialized) return FLAME_ERR_STATE;
+  const int G = c->p.graph_steps;
+  while (G > 0 && n >= G) {
+    if (!c->has_graph[c->parity]) {
+      cudaError_t e = capture_graph(c, c->parity);
+      if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    cudaError_t e = cudaGraphLaunch(c->graph[c->parity], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    const long long before = c->step;
+    c->step += G;
+    n -= G;
+    if (c->p.check_every > 0 && c->step / c->p.check_every != before / c->p.check_every) {
+      st = sync_and_check(c);
+      if (st != FLAME_OK) return st;
+    }
+  }
   for (int i = 0; i < n; ++i) {
     cudaError_t e = flame::launch_step(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
@@ -277,6 +317,15 @@ flame_status flame_populations(flame_ctx* c, double* d_f) {
   if (!c->initialized) return FLAME_ERR_STATE;
   if (!d_f) return FLAME_ERR_PARAM;
   return cuda_fail(c, flame::launch_populations(c->p.storage, c->parity, c->state, c->g, c->k, d_f, c->stream));
+}
+
+flame_status flame_probe(flame_ctx* c, int nsites, const long long* d_sites, double* d_out) {
+  flame_status st = usable(c);
+  if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  if (nsites < 0 || (nsites > 0 && (!d_sites || !d_out))) return FLAME_ERR_PARAM;
+  return cuda_fail(c, flame::launch_probe(c->p.storage, c->parity, c->state, c->g, c->k, nsites, d_sites, d_out,
+                                          c->stream));
 }
 
 flame_status flame_reduce(flame_ctx* c, double* h) {
@@ -461,6 +510,8 @@ void flame_destroy(flame_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   if (c->has_plan) cufftDestroy(c->plan);
+  for (int p = 0; p < 2; ++p)
+    if (c->has_graph[p]) cudaGraphExecDestroy(c->graph[p]);
   cudaFree(c->d_flags);
   cudaFree(c->d_red);
   cudaFree(c->d_fields);

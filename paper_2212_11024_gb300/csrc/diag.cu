@@ -198,6 +198,43 @@ __global__ void populations_kernel(const T* __restrict__ pop, Grid g, StepConsts
 }
 
 
+// Moments at a list of sites (time series): out[j] = rho, u[3], B[3], J[3].
+template <class T, bool ODD>
+__global__ void probe_kernel(const T* __restrict__ pop, Grid g, StepConsts k, int n, const long long* __restrict__ sites,
+                             double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const long long sl = sites[j];
+  if (sl < 0 || sl >= g.n3) {
+    for (int v = 0; v < 10; ++v) out[(long long)j * 10 + v] = nan("");
+    return;
+  }
+  const int site = (int)sl;
+  const int x = site % g.nx, y = (site / g.nx) % g.ny, z = site / (g.nx * g.ny);
+  const Nbr nb = make_nbr(x, y, z, g);
+  double sf[kQ], sg[3][kM];
+  load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
+  const SiteMoments m = site_moments(sf, sg, k);
+  double* o = out + (long long)j * 10;
+  o[0] = m.rho;
+  for (int a = 0; a < 3; ++a) {
+    o[1 + a] = m.U[a];
+    o[4 + a] = m.B[a];
+    o[7 + a] = m.J[a];
+  }
+}
+
+template <class T>
+cudaError_t probe_t(int odd, const void* pop, Grid g, const StepConsts& k, int n, const long long* sites, double* out,
+                    cudaStream_t s) {
+  const int tb = 64, nb = (n + tb - 1) / tb;
+  if (odd)
+    probe_kernel<T, true><<<nb, tb, 0, s>>>(static_cast<const T*>(pop), g, k, n, sites, out);
+  else
+    probe_kernel<T, false><<<nb, tb, 0, s>>>(static_cast<const T*>(pop), g, k, n, sites, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // FP64 reduction of the scalar diagnostics: per block, then a fixed-order
 // final sum (deterministic).  Partial layout (kRedVals):
@@ -334,6 +371,17 @@ cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, co
     case 1: return populations_t<float>(odd, pop, g, k, f, s);
     case 2: return populations_t<__half>(odd, pop, g, k, f, s);
     case 3: return populations_t<__nv_bfloat16>(odd, pop, g, k, f, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_probe(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int n,
+                         const long long* sites, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  switch (storage) {
+    case 1: return probe_t<float>(odd, pop, g, k, n, sites, out, s);
+    case 2: return probe_t<__half>(odd, pop, g, k, n, sites, out, s);
+    case 3: return probe_t<__nv_bfloat16>(odd, pop, g, k, n, sites, out, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -41,6 +41,10 @@ constexpr int kRedVals = 17;
 // kRedBlocksMax * kRedVals doubles of scratch).
 constexpr int kRedBlocksMax = 1024;
 
+// Moments of the listed sites: out[10 j + (rho, u[3], B[3], J[3])].
+cudaError_t launch_probe(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int n,
+                         const long long* sites, double* out, cudaStream_t s);
+
 cudaError_t launch_reduce(int storage, int odd, const void* pop, Grid g, const StepConsts& k, int nblocks,
                           double* partials, double* out, cudaStream_t s);
 

@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("tau_nu", ctypes.c_double), ("tau_eta", ctypes.c_double), ("d_i", ctypes.c_double),
         ("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("B_ref", ctypes.c_double * 3),
         ("init_noneq", ctypes.c_int), ("check_every", ctypes.c_int), ("strict_cfl", ctypes.c_int),
+        ("graph_steps", ctypes.c_int),
     ]
 
 
@@ -84,6 +85,7 @@ def _lib():
             "flame_status_string": (ctypes.c_char_p, [i]),
             "flame_lattice": (i, [P(i), P(i)]),
             "flame_reduce_static": (i, [vp, i, vp]),
+            "flame_probe": (i, [vp, i, vp, vp]),
             "flame_step_adjoint": (i, [vp, vp, i, vp, vp, vp]),
             "flame_init_adjoint": (i, [vp, vp, vp, vp, vp, vp, vp]),
         }
@@ -109,7 +111,7 @@ def lattice():
 
 
 def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
-                init_noneq=True, check_every=0, strict_cfl=False) -> Params:
+                init_noneq=True, check_every=0, strict_cfl=False, graph_steps=0) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.tau_nu, p.tau_eta, p.d_i = float(tau_nu), float(tau_eta), float(d_i)
@@ -118,6 +120,7 @@ def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_re
     for a in range(3):
         p.B_ref[a] = float(B_ref[a])
     p.init_noneq, p.check_every, p.strict_cfl = int(bool(init_noneq)), int(check_every), int(bool(strict_cfl))
+    p.graph_steps = int(graph_steps)
     return p
 
 
@@ -134,7 +137,7 @@ class Flame:
     """One periodic Hall-MHD lattice on one GPU (a flame_ctx plus its state)."""
 
     def __init__(self, nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
-                 init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None):
+                 init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None, graph_steps=0):
         import torch
 
         if not torch.cuda.is_available():
@@ -143,7 +146,7 @@ class Flame:
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.p = make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage, rho0, B_ref, init_noneq, check_every,
-                             strict_cfl)
+                             strict_cfl, graph_steps)
         self.shape = (int(nz), int(ny), int(nx))
         self.n3 = int(nx) * int(ny) * int(nz)
         nbytes = state_bytes(self.p)
@@ -214,6 +217,16 @@ class Flame:
                        J=t.empty((3,) + self.shape, dtype=t.float64, device=self.device))
         _check(self._lib.flame_moments(self._ctx_or_raise(), self._ptr(out.get("rho")), self._ptr(out.get("u")),
                                        self._ptr(out.get("B")), self._ptr(out.get("J"))), "flame_moments")
+        return out
+
+    def probe(self, sites, out=None):
+        """Moments at linear site indices (CUDA int64 tensor): FP64 [n, 10] =
+        rho, u[3], B[3], J[3].  Asynchronous; `out` may be a preallocated slice."""
+        t = self.torch
+        n = int(sites.numel())
+        if out is None:
+            out = t.empty((n, 10), dtype=t.float64, device=self.device)
+        _check(self._lib.flame_probe(self._ctx_or_raise(), n, self._ptr(sites), self._ptr(out)), "flame_probe")
         return out
 
     def populations(self):

@@ -234,3 +234,59 @@ def test_full_size_sampled_sites_256():
     for ax in "xyz":
         assert abs(s1["B_" + ax] - s0["B_" + ax]) < 1e-5
     sim.close()
+
+
+def test_probe_and_graph_stepping():
+    """flame_probe returns the moments of the listed sites (invalid index ->
+    NaN); graph_steps replays give bit-identical states to single launches
+    (odd remainders and both starting parities)."""
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    shape = (6, 7, 40)
+    nz, ny, nx = shape
+    u, B = turbulence(shape, 8, 0.05)
+    a = Flame(nx, ny, nz, 0.56, 0.6, 1.2, storage="bf16")
+    b = Flame(nx, ny, nz, 0.56, 0.6, 1.2, storage="bf16", graph_steps=8)
+    for s in (a, b):
+        s.init(None, u, B)
+    for n in (3, 37, 20):
+        a.step(n)
+        b.step(n)
+    assert a.info()["step"] == b.info()["step"] == 60
+    pa, pb = a.populations(), b.populations()
+    assert torch.equal(pa, pb)
+    m = a.moments()
+    sites = torch.tensor([0, 17, nx * ny * nz - 1, nx * ny * nz], dtype=torch.int64, device="cuda")
+    pr = a.probe(sites).cpu().numpy()
+    for j, sl in enumerate([0, 17, nx * ny * nz - 1]):
+        z, r = divmod(sl, nx * ny)
+        y, x = divmod(r, nx)
+        want = [m["rho"][z, y, x]] + [m[k][c, z, y, x] for k in ("u", "B", "J") for c in range(3)]
+        assert np.allclose(pr[j], [float(v) for v in want], rtol=0, atol=1e-15)
+    assert np.isnan(pr[3]).all()
+    a.close()
+    b.close()
+
+
+def test_three_mode_validation_second_order():
+    """Sec. 4.1 three-mode solution (Ma = 0.05, nu = 7e-3, eps_H = 1), one
+    fifth of a period: the FP32 GPU path against the exact solution at N = 16
+    and 32 (the oracle's errors are 8.4 % and 2.0 %) and N = 64; the error
+    falls as N^-2."""
+    from paper_2212_11024_gb300 import Flame
+    from paper_2212_11024_gb300 import validation as V
+    errs = []
+    for N in (16, 32, 64):
+        s = V.lattice_setup(N, 0.05, 7e-3)
+        u, B = V.initial_fields(N, s["U0"], s["alpha_p"])
+        sim = Flame(N, N, N, s["tau_nu"], s["tau_eta"], s["d_i"], B_ref=(0, 0, s["U0"]), graph_steps=16)
+        sim.init(None, u, B)
+        steps = int(round(s["period"] / 5))
+        sim.step(steps)
+        got = sim.moments()["u"][:, 0, 0, 0].cpu().numpy()
+        sim.close()
+        ue = V.exact_origin([steps], s)[0]
+        errs.append(np.linalg.norm(got - ue) / np.linalg.norm(ue))
+    assert 0.07 < errs[0] < 0.1 and 0.015 < errs[1] < 0.025, errs
+    r = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(r > 3.4) and np.all(r < 5.0), (errs, r)
