@@ -56,6 +56,17 @@ typedef enum {
 
 typedef enum { FLAME_FP32 = 1, FLAME_FP16 = 2, FLAME_BF16 = 3 } flame_storage;
 
+/* Collision scheme.  FLAME_SCHEME is the paper's (central-moment fluid,
+ * Sec. 3.1.2; Hall BGK magnetic with the current from the magnetic
+ * moments, Sec. 3.2).  The others are the variants the paper names:
+ * FLAME_BGK_FLUID  fluid collision f* = f - omega (f - f^mhd(0)) (Sec. 3.1.1);
+ * FLAME_EMHD       electron MHD: U neglected against alpha_H J in the
+ *                  magnetic equilibrium (end of Sec. 5);
+ * FLAME_FD_CURRENT J from the second-order central-difference curl of the
+ *                  pre-collision B (one extra pass writing B per step; the
+ *                  paper contrasts this with its moment-based current). */
+typedef enum { FLAME_SCHEME = 0, FLAME_BGK_FLUID = 1, FLAME_EMHD = 2, FLAME_FD_CURRENT = 3 } flame_variant;
+
 typedef struct {
     int nx, ny, nz;   /* lattice size, each >= 1                                          */
     double tau_nu;    /* fluid relaxation time 1/omega = nu/c_s^2 + 1/2 > 1/2 (Sec. 3.1.1) */
@@ -73,6 +84,8 @@ typedef struct {
     int graph_steps;  /* 0: one kernel launch per step; even G > 0: flame_step replays a
                          captured CUDA graph of G steps for each whole chunk of G steps
                          (removes launch overhead on small lattices)                    */
+    int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
+                         entry points support FLAME_SCHEME only                          */
 } flame_params;
 
 typedef struct {

@@ -72,6 +72,7 @@ def _load():
             "oracle_geq_hall": (None, [P, P, P, d, P]),
             "oracle_site_collide": (i, [P, d, d, d, i, P, P]),
             "oracle_step": (ctypes.c_long, [i, i, i, d, d, d, i, i, P, P]),
+            "oracle_step_variant": (ctypes.c_long, [i, i, i, d, d, d, i, i, i, P, P, P]),
             "oracle_init": (i, [i, i, i, d, d, d, P, P, P, P, P, i, P]),
             "oracle_moments": (None, [i, i, i, d, d, P, P, P, P, P]),
             "oracle_lattice": (None, [IP, P, IP, P]),
@@ -224,6 +225,24 @@ def step(p: Params, pop, nsteps=1, literal=True, scratch=None):
                               _p(pop), _p(scratch))
     if bad:
         raise ArithmeticError(f"{bad} singular central-moment solves")
+    return pop
+
+
+VARIANTS = {"flame": 0, "bgk": 1, "emhd": 2, "fd_current": 3}
+
+
+def step_variant(p: Params, pop, nsteps=1, variant="bgk", literal=True):
+    """Advance pop in place with a scheme variant: "bgk" (BGK fluid collision),
+    "emhd" (electron MHD magnetic equilibrium), "fd_current" (J from the
+    central-difference curl of B), or "flame" (the paper's scheme)."""
+    assert pop.shape == (NPOP,) + p.shape and pop.dtype == np.float64 and pop.flags["C_CONTIGUOUS"]
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    scratch = np.empty_like(pop)
+    bfield = np.empty((3,) + p.shape)
+    bad = _load().oracle_step_variant(p.nx, p.ny, p.nz, p.tau_nu, p.tau_eta, p.d_i, int(literal), v, int(nsteps),
+                                      _p(pop), _p(scratch), _p(bfield))
+    if bad:
+        raise ArithmeticError(f"{bad} singular solves")
     return pop
 
 

@@ -479,6 +479,50 @@ int oracle_site_collide(const double in[NPOP], double tau_nu, double tau_eta, do
     return rc;
 }
 
+/* Scheme variants (not the paper's default scheme):
+ *   1  BGK fluid collision f* = f - omega (f - f^mhd(0)) (Sec. 3.1.1, eq.
+ *      collision; the central-moment operator with S = omega I);
+ *   2  electron MHD: U neglected against alpha_H J in the magnetic
+ *      equilibrium (the extension named at the end of Sec. 5), i.e. V =
+ *      -alpha_H J and the current system with U = 0;
+ *   3  current from a finite-difference stencil: J = periodic central-
+ *      difference curl of the pre-collision B field (Jfd, supplied by the
+ *      caller), used in the Hall equilibrium instead of the 3x3 solve.
+ * Variant 0 is oracle_site_collide. */
+int oracle_site_collide_variant(const double in[NPOP], double tau_nu, double tau_eta, double d_i,
+                                int literal, int variant, const double Jfd[3], double out[NPOP]) {
+    double omega = 1.0 / tau_nu, omegaB = 1.0 / tau_eta;
+    double rho, U[3], B[3], Lam[9], J[3];
+    const double zero[3] = {0.0, 0.0, 0.0};
+    site_moments(in, &rho, U, B, Lam);
+    int rc = 0;
+    if (variant == 3) {
+        for (int a = 0; a < 3; ++a) J[a] = Jfd[a];
+    } else {
+        rc = oracle_current(literal, Lam, variant == 2 ? zero : U, B, omegaB, d_i, J);
+    }
+    double feq[NQ], lor[NQ];
+    if (literal)
+        oracle_feq_hermite(rho, U, feq);
+    else
+        oracle_feq_product(rho, U, feq);
+    oracle_lorentz(B, lor);
+    for (int i = 0; i < NQ; ++i) feq[i] += lor[i];
+    if (variant == 1) {
+        for (int i = 0; i < NQ; ++i) out[i] = in[i] - omega * (in[i] - feq[i]);
+    } else if (literal) {
+        double S[NQ];
+        for (int j = 0; j < NQ; ++j) S[j] = (j >= 4 && j <= 8) ? omega : 1.0;
+        rc |= oracle_collide_cm_literal(in, feq, U, S, out);
+    } else {
+        oracle_collide_cm_factored(in, feq, U, omega, out);
+    }
+    double geq[3 * NM];
+    oracle_geq_hall(B, variant == 2 ? zero : U, J, d_i, geq);
+    for (int q = 0; q < 3 * NM; ++q) out[NQ + q] = in[NQ + q] - omegaB * (in[NQ + q] - geq[q]);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Grid-level driver                                                   */
 /* ------------------------------------------------------------------ */
@@ -544,6 +588,56 @@ static double cdiff(const double *F, int a, int x, int y, int z, int nx, int ny,
     p[a] = wrap(p[a] + 1, n[a]);
     m[a] = wrap(m[a] - 1, n[a]);
     return 0.5 * (F[site_index(p[0], p[1], p[2], nx, ny)] - F[site_index(m[0], m[1], m[2], nx, ny)]);
+}
+
+/* oracle_step for a scheme variant (see oracle_site_collide_variant).  For
+ * variant 3, B is computed at every site first and J = curl B by periodic
+ * central differences.  `bfield` (3 N3 doubles) is scratch, may be NULL for
+ * the other variants. */
+long oracle_step_variant(int nx, int ny, int nz, double tau_nu, double tau_eta, double d_i, int literal,
+                         int variant, int nsteps, double *pop, double *post, double *bfield) {
+    build_tables();
+    long n3 = (long)nx * ny * nz;
+    long bad = 0;
+    for (int step = 0; step < nsteps; ++step) {
+        if (variant == 3) {
+#pragma omp parallel for schedule(static)
+            for (long s = 0; s < n3; ++s)
+                for (int b = 0; b < 3; ++b) {
+                    double v = 0.0;
+                    for (int i = 0; i < NM; ++i) v += pop[(NQ + b * NM + i) * n3 + s];
+                    bfield[b * n3 + s] = v;
+                }
+        }
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+        for (long s = 0; s < n3; ++s) {
+            double in[NPOP], out[NPOP], J[3] = {0.0, 0.0, 0.0};
+            for (int q = 0; q < NPOP; ++q) in[q] = pop[q * n3 + s];
+            if (variant == 3) {
+                int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long)nx * ny));
+                double d[3][3];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) d[a][b] = cdiff(bfield + b * n3, a, x, y, z, nx, ny, nz);
+                J[0] = d[1][2] - d[2][1];
+                J[1] = d[2][0] - d[0][2];
+                J[2] = d[0][1] - d[1][0];
+            }
+            if (oracle_site_collide_variant(in, tau_nu, tau_eta, d_i, literal, variant, J, out) != 0) ++bad;
+            for (int q = 0; q < NPOP; ++q) post[q * n3 + s] = out[q];
+        }
+#pragma omp parallel for schedule(static)
+        for (long s = 0; s < n3; ++s) {
+            int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long)nx * ny));
+            for (int q = 0; q < NPOP; ++q) {
+                int c[3];
+                pop_velocity(q, c);
+                long src = site_index(wrap(x - c[0], nx), wrap(y - c[1], ny), wrap(z - c[2], nz),
+                                      nx, ny);
+                pop[q * n3 + s] = post[q * n3 + src];
+            }
+        }
+    }
+    return bad;
 }
 
 /* Initial populations from macroscopic fields (the paper only states the

@@ -69,3 +69,48 @@ def scalars(rho, u, B, J):
         enstrophy=enstrophy(u),
         u_max=float(np.sqrt((u * u).sum(axis=0)).max()),
     )
+
+
+def energy_budget(u, B, nu, eta, nshell, d_i=0.0):
+    """(E, S, D) of Sec. 4.3 (eq. mhd_en_trans), numpy FP64, written mode by
+    mode from the definitions: F = FFT/N3, k = 2 pi m/N (Nyquist k = 0 for
+    derivatives), J = curl B spectrally, V = u - d_i J; S(n), D(n) sum the
+    modes with round|m| < n; E(n) = 1/2 sum_{shell n} |F(u)|^2 + |F(B)|^2."""
+    shape = u.shape[1:]
+    n3 = float(np.prod(shape))
+    ks = []
+    for ax, n in zip((2, 1, 0), (shape[2], shape[1], shape[0])):
+        m = np.fft.fftfreq(n, 1.0 / n)
+        k = 2 * np.pi * m / n
+        if n % 2 == 0:
+            k[n // 2] = 0.0
+        sh = [1, 1, 1]
+        sh[ax] = n
+        ks.append(k.reshape(sh))
+    kx, ky, kz = ks
+    F = lambda f: np.fft.fftn(f) / n3
+    iF = lambda G: np.real(np.fft.ifftn(G)) * n3
+    uh = [F(u[c]) for c in range(3)]
+    Bh = [F(B[c]) for c in range(3)]
+    J = np.stack([iF(1j * (ky * Bh[2] - kz * Bh[1])), iF(1j * (kz * Bh[0] - kx * Bh[2])),
+                  iF(1j * (kx * Bh[1] - ky * Bh[0]))])
+    ugu = np.stack([u[0] * iF(1j * kx * uh[b]) + u[1] * iF(1j * ky * uh[b]) + u[2] * iF(1j * kz * uh[b])
+                    for b in range(3)])
+    JxB = np.cross(J, B, axis=0)
+    V = u - d_i * J
+    VxB = np.cross(V, B, axis=0)
+    Wh = [F(VxB[c]) for c in range(3)]
+    ind = [1j * (ky * Wh[2] - kz * Wh[1]), 1j * (kz * Wh[0] - kx * Wh[2]), 1j * (kx * Wh[1] - ky * Wh[0])]
+    T = sum(np.real(np.conj(uh[c]) * (F(ugu[c]) - F(JxB[c]))) - np.real(np.conj(Bh[c]) * ind[c]) for c in range(3))
+    k2 = kx * kx + ky * ky + kz * kz
+    dis = sum(nu * k2 * np.abs(uh[c]) ** 2 + eta * k2 * np.abs(Bh[c]) ** 2 for c in range(3))
+    en = 0.5 * sum(np.abs(uh[c]) ** 2 + np.abs(Bh[c]) ** 2 for c in range(3))
+    idx = shell_index(shape)
+    E = np.zeros(nshell)
+    S = np.zeros(nshell)
+    D = np.zeros(nshell)
+    for n in range(nshell):
+        E[n] = en[idx == n].sum()
+        S[n] = T[idx < n].sum()
+        D[n] = dis[idx < n].sum()
+    return E, S, D

@@ -32,6 +32,7 @@ struct flame_ctx {
   int nshell_cap;
   cufftHandle plan;
   bool has_plan;
+  float* d_bfield;           // 3 N3 floats, FLAME_FD_CURRENT only
   cudaGraphExec_t graph[2];  // graph_steps launches starting at parity 0 / 1
   bool has_graph[2];
   double* d_adj_partials;  // adjoint_partials_needed doubles
@@ -59,6 +60,7 @@ flame_status check_params(const flame_params* p) {
   if (elem_bytes(p->storage) == 0) return FLAME_ERR_PARAM;
   if (p->check_every < 0) return FLAME_ERR_PARAM;
   if (p->graph_steps < 0 || (p->graph_steps & 1)) return FLAME_ERR_PARAM;
+  if (p->variant < FLAME_SCHEME || p->variant > FLAME_FD_CURRENT) return FLAME_ERR_PARAM;
   return FLAME_OK;
 }
 
@@ -186,6 +188,12 @@ flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state,
     delete c;
     return FLAME_ERR_CUDA;
   }
+  if (p->variant == FLAME_FD_CURRENT &&
+      cudaMalloc(&c->d_bfield, 3 * sizeof(float) * (size_t)p->nx * p->ny * p->nz) != cudaSuccess) {
+    cudaFree(c->d_flags);
+    delete c;
+    return FLAME_ERR_CUDA;
+  }
   c->k.omega = (float)(1.0 / p->tau_nu);
   c->k.omegaB = (float)(1.0 / p->tau_eta);
   c->k.alphaH = (float)p->d_i;
@@ -242,7 +250,8 @@ static cudaError_t capture_graph(flame_ctx* c, int parity) {
   if (e == cudaSuccess) {
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < c->p.graph_steps && le == cudaSuccess; ++i)
-      le = flame::launch_step(c->p.storage, parity ^ (i & 1), c->state, c->g, c->k, c->d_flags, cs);
+      le = flame::launch_step(c->p.storage, parity ^ (i & 1), c->state, c->g, c->k, c->d_flags, cs, c->p.variant,
+                              c->d_bfield);
     e = cudaStreamEndCapture(cs, &graph);
     if (le != cudaSuccess) e = le;
   }
@@ -275,7 +284,8 @@ flame_status flame_step(flame_ctx* c, int n) {
     }
   }
   for (int i = 0; i < n; ++i) {
-    cudaError_t e = flame::launch_step(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream);
+    cudaError_t e = flame::launch_step(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream,
+                                       c->p.variant, c->d_bfield);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->parity ^= 1;
     ++c->step;
@@ -468,6 +478,7 @@ flame_status flame_set_state(flame_ctx* c, const void* d_src, long long step, in
 flame_status flame_step_adjoint(flame_ctx* c, const void* d_state, int parity, const float* d_adj_in,
                                 float* d_adj_out, double* d_ddi) {
   if (!c || !d_state || !d_adj_in || !d_adj_out || !d_ddi) return FLAME_ERR_PARAM;
+  if (c->p.variant != FLAME_SCHEME) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
   if (parity != 0 && parity != 1) return FLAME_ERR_STATE;
   if (d_adj_in == d_adj_out) return FLAME_ERR_PARAM;
@@ -486,6 +497,7 @@ flame_status flame_step_adjoint(flame_ctx* c, const void* d_state, int parity, c
 flame_status flame_init_adjoint(flame_ctx* c, const double* d_u, const double* d_B, const float* d_adj0,
                                 double* d_ubar, double* d_Bbar, double* d_ddi) {
   if (!c || !d_u || !d_B || !d_adj0 || !d_ddi || (!d_ubar && !d_Bbar)) return FLAME_ERR_PARAM;
+  if (c->p.variant != FLAME_SCHEME) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
   cudaError_t e;
   if (!c->d_adj_partials) {
@@ -519,6 +531,7 @@ void flame_destroy(flame_ctx* c) {
   cudaFree(c->d_shells);
   cudaFree(c->d_adj_partials);
   cudaFree(c->d_adj_ws);
+  cudaFree(c->d_bfield);
   delete c;
 }
 

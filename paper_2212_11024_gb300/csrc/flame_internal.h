@@ -21,9 +21,16 @@ struct Grid {
   long long n3;
 };
 
-// storage: 1 FP32, 2 FP16, 3 BF16 (flame_storage)
+// Scheme variants (flame_variant).
+constexpr int kVarFlame = 0;      // the paper's scheme
+constexpr int kVarBgkFluid = 1;   // BGK fluid collision
+constexpr int kVarEmhd = 2;       // electron MHD magnetic equilibrium
+constexpr int kVarFdCurrent = 3;  // J from the central-difference curl of B
+
+// storage: 1 FP32, 2 FP16, 3 BF16 (flame_storage).  Bfd: 3 N3 floats of
+// scratch, required by kVarFdCurrent only.
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                        cudaStream_t s);
+                        cudaStream_t s, int variant = kVarFlame, float* Bfd = nullptr);
 
 cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
                         const double* u, const double* B, const double* gu, const double* gB,

@@ -36,9 +36,12 @@ namespace {
 constexpr int kStepThreads = 256;
 constexpr int kStepMinBlocks = 3;
 
-template <class T, bool ODD>
+// VAR selects the scheme: kVarFlame (the paper's), kVarBgkFluid, kVarEmhd or
+// kVarFdCurrent (flame_internal.h); Bfd is the pre-collision B - B_ref field
+// written by bfield_kernel, read only by kVarFdCurrent.
+template <class T, bool ODD, int VAR>
 __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
-    step_kernel(Slots<T> P, Grid g, StepConsts k, unsigned* __restrict__ flag) {
+    step_kernel(Slots<T> P, Grid g, StepConsts k, unsigned* __restrict__ flag, const float* __restrict__ Bfd) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -127,20 +130,33 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
   }
 
   // a4: J + s J x B = y, y = -(omega_B/C^2)(A - 2 U x B), s = 2 alpha_H omega_B / C^2.
-  const float gq = 4.f * k.omegaB;
-  const float A[3] = {lam[1][2] - lam[2][1], lam[2][0] - lam[0][2], lam[0][1] - lam[1][0]};
-  const float uxb[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2], U[0] * B[1] - U[1] * B[0]};
-  const float yv[3] = {-gq * (A[0] - 2.f * uxb[0]), -gq * (A[1] - 2.f * uxb[1]), -gq * (A[2] - 2.f * uxb[2])};
-  const float sH = 2.f * k.alphaH * gq;
-  const float yxb[3] = {yv[1] * B[2] - yv[2] * B[1], yv[2] * B[0] - yv[0] * B[2], yv[0] * B[1] - yv[1] * B[0]};
-  const float yb = yv[0] * B[0] + yv[1] * B[1] + yv[2] * B[2];
-  const float b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-  const float iden = 1.f / (1.f + sH * sH * b2);
+  // (Electron MHD: U is neglected against alpha_H J, here and in g^Hall(0).)
   float V[3];
+  if constexpr (VAR == kVarFdCurrent) {
+    // J = periodic central-difference curl of the pre-collision field
+    const long long n3 = g.n3;
+    auto Bn = [&](int b, int off) { return Bfd[b * n3 + site + off]; };
+    const float J[3] = {0.5f * ((Bn(2, nb.yp) - Bn(2, nb.ym)) - (Bn(1, nb.zp) - Bn(1, nb.zm))),
+                        0.5f * ((Bn(0, nb.zp) - Bn(0, nb.zm)) - (Bn(2, nb.xp) - Bn(2, nb.xm))),
+                        0.5f * ((Bn(1, nb.xp) - Bn(1, nb.xm)) - (Bn(0, nb.yp) - Bn(0, nb.ym)))};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float J = (yv[a] - sH * yxb[a] + sH * sH * yb * B[a]) * iden;
-    V[a] = U[a] - k.alphaH * J;
+    for (int a = 0; a < 3; ++a) V[a] = U[a] - k.alphaH * J[a];
+  } else {
+    const float Ue[3] = {VAR == kVarEmhd ? 0.f : U[0], VAR == kVarEmhd ? 0.f : U[1], VAR == kVarEmhd ? 0.f : U[2]};
+    const float gq = 4.f * k.omegaB;
+    const float A[3] = {lam[1][2] - lam[2][1], lam[2][0] - lam[0][2], lam[0][1] - lam[1][0]};
+    const float uxb[3] = {Ue[1] * B[2] - Ue[2] * B[1], Ue[2] * B[0] - Ue[0] * B[2], Ue[0] * B[1] - Ue[1] * B[0]};
+    const float yv[3] = {-gq * (A[0] - 2.f * uxb[0]), -gq * (A[1] - 2.f * uxb[1]), -gq * (A[2] - 2.f * uxb[2])};
+    const float sH = 2.f * k.alphaH * gq;
+    const float yxb[3] = {yv[1] * B[2] - yv[2] * B[1], yv[2] * B[0] - yv[0] * B[2], yv[0] * B[1] - yv[1] * B[0]};
+    const float yb = yv[0] * B[0] + yv[1] * B[1] + yv[2] * B[2];
+    const float b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const float iden = 1.f / (1.f + sH * sH * b2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float J = (yv[a] - sH * yxb[a] + sH * sH * yb * B[a]) * iden;
+      V[a] = Ue[a] - k.alphaH * J;
+    }
   }
 
   // a6: magnetic BGK towards g^Hall(0); deviations: rest dB_b, face
@@ -219,9 +235,12 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
       const int cx = px - 1, cy = py - 1;
       const float exy = ex[px] + ey[py] + ex[px] * ey[py];
       const float g = fmaf(rho, exy, rho);
-      const float A0 = (Dxx * p2[px]) * p0y[py] + (Dyy * p2[py]) * p0x[px] + (Dxy * p1x[px]) * p1y[py];
-      const float A1 = (Dxz * p1x[px]) * p0y[py] + (Dyz * p1y[py]) * p0x[px];
-      const float A2 = (Dzz * p0x[px]) * p0y[py];
+      // BGK fluid collision: no projected non-equilibrium part; the result is
+      // blended with the pre-collision populations below.
+      const float A0 = VAR == kVarBgkFluid ? 0.f
+                                           : (Dxx * p2[px]) * p0y[py] + (Dyy * p2[py]) * p0x[px] + (Dxy * p1x[px]) * p1y[py];
+      const float A1 = VAR == kVarBgkFluid ? 0.f : (Dxz * p1x[px]) * p0y[py] + (Dyz * p1y[py]) * p0x[px];
+      const float A2 = VAR == kVarBgkFluid ? 0.f : (Dzz * p0x[px]) * p0y[py];
       float Lxy = Lbase;
       if (cx != 0) Lxy += LA;
       if (cy != 0) Lxy += LB;
@@ -233,7 +252,11 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
       const float Z1 = g * e1z + A0 * q10 + 3.f * A1 + Lz1;
       const float Z2 = g * e2z + A0 * q20 + A1 * q21 + 4.5f * A2 + LZ;
       const float tz = Z0 + Z2;
-      const float vz[3] = {tz - Z1, Z0, tz + Z1};
+      float vz[3] = {tz - Z1, Z0, tz + Z1};
+      if constexpr (VAR == kVarBgkFluid) {
+#pragma unroll
+        for (int pz = 0; pz < 3; ++pz) vz[pz] = (1.f - k.omega) * s[px + 3 * py + 9 * pz] + k.omega * vz[pz];
+      }
 #pragma unroll
       for (int pz = 0; pz < 3; ++pz) {
         const int i = idx27(px, py, pz);
@@ -244,15 +267,58 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
 }
 
 
+// B - B_ref of the pre-collision populations at every site (FP32), for the
+// finite-difference current variant.
+template <class T, bool ODD>
+__global__ void bfield_kernel(Slots<T> P, Grid g, float* __restrict__ Bfd) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const int site = (z * g.ny + y) * g.nx + x;
+  const Nbr nb = make_nbr(x, y, z, g);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < kM; ++i)
+      v += (i == 0 ? 0.25f : 0.125f) *
+           Codec<T>::dec(P.p[mslot(b, ODD ? opp7(i) : i)][site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i))]);
+    Bfd[(long long)b * g.n3 + site] = v;
+  }
+}
+
+template <class T, int VAR>
+void step_launch(int odd, const Slots<T>& P, Grid g, const StepConsts& k, unsigned* flag, const float* Bfd, dim3 gr,
+                 dim3 b, cudaStream_t s) {
+  if (odd)
+    step_kernel<T, true, VAR><<<gr, b, 0, s>>>(P, g, k, flag, Bfd);
+  else
+    step_kernel<T, false, VAR><<<gr, b, 0, s>>>(P, g, k, flag, Bfd);
+}
+
 template <class T>
-cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s) {
+cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, int variant, float* Bfd,
+                   cudaStream_t s) {
   const dim3 b = site_block(g, kStepThreads), gr = site_grid(g, b);
   Slots<T> P;
   for (int q = 0; q < kPop; ++q) P.p[q] = static_cast<T*>(pop) + (size_t)q * (size_t)g.n3;
-  if (odd)
-    step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, flag);
-  else
-    step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, flag);
+  switch (variant) {
+    case kVarFlame: step_launch<T, kVarFlame>(odd, P, g, k, flag, nullptr, gr, b, s); break;
+    case kVarBgkFluid: step_launch<T, kVarBgkFluid>(odd, P, g, k, flag, nullptr, gr, b, s); break;
+    case kVarEmhd: step_launch<T, kVarEmhd>(odd, P, g, k, flag, nullptr, gr, b, s); break;
+    case kVarFdCurrent: {
+      if (!Bfd) return cudaErrorInvalidValue;
+      const dim3 bb = site_block(g, 128), gb = site_grid(g, bb);
+      if (odd)
+        bfield_kernel<T, true><<<gb, bb, 0, s>>>(P, g, Bfd);
+      else
+        bfield_kernel<T, false><<<gb, bb, 0, s>>>(P, g, Bfd);
+      step_launch<T, kVarFdCurrent>(odd, P, g, k, flag, Bfd, gr, b, s);
+      break;
+    }
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -260,11 +326,11 @@ cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fl
 }  // namespace
 
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                        cudaStream_t s) {
+                        cudaStream_t s, int variant, float* Bfd) {
   switch (storage) {
-    case 1: return step_t<float>(odd, pop, g, k, flag, s);
-    case 2: return step_t<__half>(odd, pop, g, k, flag, s);
-    case 3: return step_t<__nv_bfloat16>(odd, pop, g, k, flag, s);
+    case 1: return step_t<float>(odd, pop, g, k, flag, variant, Bfd, s);
+    case 2: return step_t<__half>(odd, pop, g, k, flag, variant, Bfd, s);
+    case 3: return step_t<__nv_bfloat16>(odd, pop, g, k, flag, variant, Bfd, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libflame.so")
 
 FLAME_OK, FLAME_ERR_PARAM, FLAME_ERR_CFL, FLAME_ERR_NONFINITE, FLAME_ERR_CUDA, FLAME_ERR_STATE = range(6)
 STORAGE = {"fp32": 1, "fp16": 2, "bf16": 3}
+VARIANT = {"flame": 0, "bgk": 1, "emhd": 2, "fd_current": 3}
 NSCALARS = 14
 SCALAR_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "B_x", "B_y", "B_z", "E_u", "E_B", "H_c", "J2", "u_max",
                 "divB_rms", "nonfinite"]
@@ -46,7 +47,7 @@ class Params(ctypes.Structure):
         ("tau_nu", ctypes.c_double), ("tau_eta", ctypes.c_double), ("d_i", ctypes.c_double),
         ("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("B_ref", ctypes.c_double * 3),
         ("init_noneq", ctypes.c_int), ("check_every", ctypes.c_int), ("strict_cfl", ctypes.c_int),
-        ("graph_steps", ctypes.c_int),
+        ("graph_steps", ctypes.c_int), ("variant", ctypes.c_int),
     ]
 
 
@@ -111,7 +112,7 @@ def lattice():
 
 
 def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
-                init_noneq=True, check_every=0, strict_cfl=False, graph_steps=0) -> Params:
+                init_noneq=True, check_every=0, strict_cfl=False, graph_steps=0, variant="flame") -> Params:
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.tau_nu, p.tau_eta, p.d_i = float(tau_nu), float(tau_eta), float(d_i)
@@ -121,6 +122,7 @@ def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_re
         p.B_ref[a] = float(B_ref[a])
     p.init_noneq, p.check_every, p.strict_cfl = int(bool(init_noneq)), int(check_every), int(bool(strict_cfl))
     p.graph_steps = int(graph_steps)
+    p.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
     return p
 
 
@@ -137,7 +139,8 @@ class Flame:
     """One periodic Hall-MHD lattice on one GPU (a flame_ctx plus its state)."""
 
     def __init__(self, nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
-                 init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None, graph_steps=0):
+                 init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None, graph_steps=0,
+                 variant="flame"):
         import torch
 
         if not torch.cuda.is_available():
@@ -146,7 +149,7 @@ class Flame:
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.p = make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage, rho0, B_ref, init_noneq, check_every,
-                             strict_cfl, graph_steps)
+                             strict_cfl, graph_steps, variant)
         self.shape = (int(nz), int(ny), int(nx))
         self.n3 = int(nx) * int(ny) * int(nz)
         nbytes = state_bytes(self.p)

@@ -290,3 +290,52 @@ def test_three_mode_validation_second_order():
     assert 0.07 < errs[0] < 0.1 and 0.015 < errs[1] < 0.025, errs
     r = np.array(errs[:-1]) / np.array(errs[1:])
     assert np.all(r > 3.4) and np.all(r < 5.0), (errs, r)
+
+
+@pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
+def test_scheme_variants_match_oracle(variant):
+    """The BGK-fluid, electron-MHD and finite-difference-current variants of
+    the fused step (FP32 storage, 12 steps, ragged grid with a mean field) vs
+    the oracle's variants."""
+    from paper_2212_11024_gb300 import Flame
+    shape = (6, 5, 40)
+    nz, ny, nx = shape
+    u, B = turbulence(shape, 19, 0.05)
+    Bref = (0.0, 0.02, 0.06)
+    B = B + np.array(Bref)[:, None, None, None]
+    sim = Flame(nx, ny, nz, 0.56, 0.61, 1.4, B_ref=Bref, variant=variant, graph_steps=4)
+    sim.init(None, u, B)
+    sim.step(12)
+    fg = sim.populations().cpu().numpy()
+    sim.close()
+    p = O.Params(nx, ny, nz, 0.56, 0.61, 1.4)
+    fo = O.init(p, None, u, B)
+    O.step_variant(p, fo, 12, variant)
+    rest = rest_populations(shape, 1.0, Bref)
+    assert rel_dev_err(fg, fo, rest, slice(0, 27)) < 1e-6
+    assert rel_dev_err(fg, fo, rest, slice(27, 48)) < 1e-6
+
+
+def test_orszag_tang_run_and_energy_budget():
+    """Orszag-Tang vortex (Sec. 4.3) at 32^3 (U0 = 0.05/sqrt(3), B0 = 0.8 U0,
+    tau = 0.6), 40 steps through the library; the budget of the resulting
+    fields computed on the GPU (budget.energy_budget on CUDA tensors) equals
+    the numpy FP64 oracle implementation on the same fields."""
+    import torch
+    from oracle import spectra as S
+    from paper_2212_11024_gb300 import Flame, budget, inputs
+    N = 32
+    u, B = inputs.orszag_tang((N, N, N), 1.0, 0.8, scale=0.05 / np.sqrt(3.0))
+    sim = Flame(N, N, N, 0.6, 0.6, 0.0)
+    sim.init(None, u, B)
+    sim.step(40)
+    m = sim.moments()
+    sim.close()
+    nu, eta = 0.1 / 3, 0.1 / 4
+    E, Sf, D = [x.cpu().numpy() for x in budget.energy_budget(m["u"], m["B"], nu, eta, 30)]
+    E0, S0, D0 = S.energy_budget(m["u"].cpu().numpy(), m["B"].cpu().numpy(), nu, eta, 30)
+    assert np.allclose(E, E0, rtol=1e-12, atol=1e-20)
+    assert np.allclose(Sf, S0, rtol=1e-9, atol=1e-16 * np.abs(S0).max())
+    assert np.allclose(D, D0, rtol=1e-12, atol=1e-20)
+    # after 40 steps energy has moved beyond the initial shells 1-2
+    assert E[3:].sum() > 1e-6 * E.sum()

@@ -461,3 +461,81 @@ def test_exact_wave_unequal_viscosity_resistivity():
     """tau_nu != tau_eta (nu != eta): the 2x2 exact solution still applies."""
     eu, eb, _ = _wave_error(32, 2, 200, 2.0, 0.1, 1e-3, tau_nu=0.7, tau_eta=0.55)
     assert eu < 4e-2 and eb < 5e-2
+
+
+# ----------------------------------------------------------- scheme variants
+def test_variant_bgk_equals_literal_bgk_limit():
+    """Variant "bgk" is the central-moment operator with S = omega I
+    (Sec. 3.1.2): the grid step equals per-site BGK collisions plus streaming,
+    in both the literal and the factored oracle modes."""
+    shape = (5, 4, 6)
+    u, B = _smooth_random(shape, 41, 0.05)
+    p = O.Params(6, 4, 5, 0.57, 0.6, 1.1)
+    a = O.init(p, None, u, B)
+    b = a.copy()
+    O.step_variant(p, a, 3, "bgk", literal=True)
+    O.step_variant(p, b, 3, "bgk", literal=False)
+    assert np.allclose(a, b, rtol=0, atol=1e-14)
+    # per-site check of one collision against f - omega (f - f^eq)
+    pop = O.init(p, None, u, B)
+    x = pop[:, 0, 0, 0]
+    f = x[:27]
+    rho = f.sum()
+    U = (f @ C) / rho
+    g = x[27:].reshape(3, 7)
+    Bv = g.sum(1)
+    feq = O.feq_hermite(rho, U) + O.lorentz(Bv)
+    S = np.full(27, 1 / 0.57)
+    assert np.allclose(O.collide_cm_literal(f, feq, U, S), f - (1 / 0.57) * (f - feq), atol=1e-15)
+
+
+def test_variant_emhd_exact_whistler():
+    """Electron MHD (end of Sec. 5): with U dropped from the magnetic
+    equilibrium the field obeys db/dt = -d_i curl(J x B0) + eta lap b, so the
+    parallel circularly polarised mode evolves as c(t) = c0 exp(-(i d_i B0
+    k^2 + eta k^2) t) whatever the flow does.  Checked after 200 steps at
+    N = 32 and 64 (diffusive scaling): second-order convergence."""
+    from paper_2212_11024_gb300 import inputs as I
+    errs = []
+    for N in (32, 64):
+        s = N / 32
+        di, B0, amp, steps = 2.0 * s, 0.1 / s, 1e-3 / s, int(200 * s * s)
+        shape = (N, 2, 2)
+        k = 2 * np.pi / N
+        u, B = I.parallel_wave(shape, 1, amp, B0, 0.5)
+        gu, gB = I.parallel_wave_gradients(shape, 1, amp, 0.5)
+        p = O.Params(2, 2, N, 0.6, 0.6, di)
+        pop = O.init(p, None, u, B, gu, gB)
+        O.step_variant(p, pop, steps, "emhd", literal=False)
+        m = O.moments(p, pop)
+        eta = 0.1 * 0.25
+        c = 0.5 * amp * np.exp(-(1j * di * B0 * k * k + eta * k * k) * steps)
+        z = np.arange(N)
+        want = np.stack([np.imag(c * np.exp(1j * k * z)), np.real(c * np.exp(1j * k * z))])
+        got = m["B"][:2, :, 0, 0]
+        errs.append(np.linalg.norm(got - want) / np.linalg.norm(want))
+    assert errs[0] < 8e-2 and 3.0 < errs[0] / errs[1] < 5.5, errs
+
+
+def test_variant_fd_current_converges_to_exact_wave():
+    """Current from the central-difference curl of B: the parallel
+    Hall-MHD wave still converges to the exact solution at second order."""
+    from oracle import exact_wave as X
+    from paper_2212_11024_gb300 import inputs as I
+    errs = []
+    for N in (16, 32, 64):
+        s = N / 32
+        di, B0, amp, steps = 2.0 * s, 0.1 / s, 1e-3 / s, int(round(200 * s * s))
+        shape = (N, 2, 2)
+        k = 2 * np.pi / N
+        ap, _ = X.alpha_pm(k, di)
+        u, B = I.parallel_wave(shape, 1, amp, B0, ap)
+        gu, gB = I.parallel_wave_gradients(shape, 1, amp, ap)
+        p = O.Params(2, 2, N, 0.6, 0.6, di)
+        pop = O.init(p, None, u, B, gu, gB)
+        O.step_variant(p, pop, steps, "fd_current", literal=False)
+        m = O.moments(p, pop)
+        ue, _ = X.fields(steps, shape, 1, B0, 0.1 / 3, 0.1 / 4, di, amp, ap * amp)
+        errs.append(X.rel_l2(m["u"], ue))
+    r = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(r > 3.0) and np.all(r < 5.5), (errs, r)
