@@ -10,6 +10,7 @@ current obtained from the magnetic non-equilibrium moments.
 - ``units``   : lattice-unit parameter mapping and the whistler CFL check.
 - ``adjoint`` : gradients of a band magnetic energy through N steps
                 (FlameBandEnergy autograd Function, sqrt(N) checkpointing).
+- ``turbulence``: decaying-turbulence runs with spectra and step throughput.
 - ``build``   : nvcc build of libflame.so for sm_103a.
 """
 from . import inputs, units
