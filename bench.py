@@ -5,8 +5,11 @@ Workload (default): 256^3 decaying Hall-MHD turbulence -- seeded random-phase
 solenoidal u and B with energy in shells 1..4 (u_rms = b_rms = 0.05, seeds 3
 and 4), rho = 1, tau_nu = tau_eta = 0.51, d_i = 0.05 * 256 = 12.8.  The
 headline is FP16 deviation storage with FP32 collision; FP32 and BF16
-storage are timed in the same run.  A step is one launch of the fused
-collide-and-stream kernel over all 256^3 sites.
+storage are timed in the same run, and FP16 / BF16 once more with the
+one-site kernel forced ("fp16/site") for comparison with the row kernel.  A
+step is one launch of the fused collide-and-stream kernel over all 256^3
+sites: the row kernel (TMA-staged x rows, two sites per thread in packed
+FP32 pairs) for 16-bit storage, the one-site kernel for FP32.
 
 Metric: MLUPS (million lattice-site updates per second) and the fraction of
 the measured HBM bandwidth reached by the step kernel, with the per-field
@@ -66,10 +69,23 @@ def hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("step.cu", "lattice.cuh", "aa.cuh"):
+    for f in ("step.cu", "step_row.cu", "lattice.cuh", "aa.cuh"):
         with open(os.path.join(ROOT, "paper_2212_11024_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def parse_variant(spec):
+    """"fp16" -> ("fp16", "auto"); "fp16/site" -> ("fp16", "site")."""
+    st, _, kern = spec.partition("/")
+    return st, (kern or "auto")
+
+
+def kernel_name(storage, kernel, n):
+    """The step kernel flame_step launches for this storage at n^3."""
+    if kernel == "auto" and storage in ("fp16", "bf16") and 64 <= n <= 512 and n % 64 == 0:
+        return f"step_row_kernel<{storage}> (TMA-staged x rows, packed FP32 pairs)"
+    return f"step_kernel<{storage}> (one site per thread)"
 
 
 def recorded_traffic(storage):
@@ -274,7 +290,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--impl", default="flame", choices=["flame", "reference"])
-    ap.add_argument("--storage", default="fp16,fp32,bf16", help="first entry is the headline")
+    ap.add_argument("--storage", default="fp16,fp32,bf16,fp16/site,bf16/site",
+                    help="first entry is the headline; '/site' forces the one-site kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the host-oracle legs (CPU baseline and the 64^3 oracle accuracy check)")
     args = ap.parse_args()
@@ -326,8 +343,9 @@ def main():
     clocks.start()
     stream = torch.cuda.current_stream(dev)
     variants = {}
-    for st in storages:
-        sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev)
+    for spec in storages:
+        st, kern = parse_variant(spec)
+        sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev, kernel=kern)
         sim.init(None, u_d, B_d)
         sim.step(args.warmup)
         barrier()
@@ -351,10 +369,11 @@ def main():
         mlups = world * sites * args.steps / (ms_max * 1e-3) / 1e6
         per_launch_s = ms / args.steps * 1e-3
         achieved = BYTES_PER_SITE[st] * sites / per_launch_s / 1e9
-        variants[st] = {"mlups": mlups, "ms_per_step": ms_max / args.steps, "achieved_gbs": achieved,
-                        "frac_of_measured_hbm": achieved / peak, "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                        "algorithmic_bytes_per_site": BYTES_PER_SITE[st], "state_gb": 48 * sites * (4 if st == "fp32" else 2) / 1e9,
-                        "status": status}
+        variants[spec] = {"mlups": mlups, "ms_per_step": ms_max / args.steps, "achieved_gbs": achieved,
+                          "frac_of_measured_hbm": achieved / peak, "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                          "algorithmic_bytes_per_site": BYTES_PER_SITE[st],
+                          "state_gb": 48 * sites * (4 if st == "fp32" else 2) / 1e9,
+                          "kernel": kernel_name(st, kern, n), "status": status}
         sim.close()
         del sim
         torch.cuda.empty_cache()
@@ -362,9 +381,10 @@ def main():
     # Accuracy at the stated step counts (outside the timed region).  The
     # 256^3 recipe is chaotic: differences e-fold every ~20-25 steps, so
     # fields are compared early, spectra by shell.
-    accuracy = {st: {} for st in storages}
+    acc_storages = [spec for spec in storages if "/" not in spec]
+    accuracy = {st: {} for st in acc_storages}
     finals = {}
-    for st in storages:
+    for st in acc_storages:
         sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev)
         sim.init(None, u_d, B_d)
         sim.step(ACC_STEPS)
@@ -376,13 +396,13 @@ def main():
         del sim
     if "fp32" in finals:
         ru, rb, rEu, rEb = finals["fp32"]
-        for st in storages:
+        for st in acc_storages:
             if st != "fp32":
                 accuracy[st]["vs_fp32_256"] = field_errors(finals[st], finals["fp32"], n, ACC_STEPS)
     finals.clear()
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
-        for st, errs in oracle_restriction_errors(storages, dev).items():
+        for st, errs in oracle_restriction_errors(acc_storages, dev).items():
             accuracy[st]["vs_oracle_64"] = errs
 
     # end to end through the public API with host buffers: H2D of the initial
@@ -390,7 +410,8 @@ def main():
     pin_u = torch.from_numpy(u_h).pin_memory()
     pin_B = torch.from_numpy(B_h).pin_memory()
     out_h = torch.empty((9, n, n, n), dtype=torch.float64).pin_memory()
-    sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=head, device=dev)
+    sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=parse_variant(head)[0], device=dev,
+                kernel=parse_variant(head)[1])
     outs = {"u": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
             "B": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
             "J": torch.empty((3, n, n, n), dtype=torch.float64, device=dev)}
@@ -435,18 +456,19 @@ def main():
                          f"{secs:.1f} s on {cores} threads"}
 
     hv = variants[head]
-    traffic = recorded_traffic(head)
+    head_st, head_kern = parse_variant(head)
+    traffic = recorded_traffic(head_st) if head_kern == "auto" else None
     line = {
         "metric": METRIC, "value": hv["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": hv["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(n, head), "n": n, "storage": head, "compute": "fp32",
+        "config": {"workload": workload_name(n, head_st), "n": n, "storage": head_st, "compute": "fp32",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"no flush: the {hv['state_gb']:.2f} GB state streamed each step exceeds the 129 MB L2"},
         "roofline": {"bound": "hbm", "achieved": hv["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": hv["achieved_gbs"] / peak, "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": hv["algorithmic_bytes_per_site"] * n ** 3,
-                     "kernel": f"step_kernel<{head}> (fused collide + AA stream)",
+                     "kernel": kernel_name(head_st, head_kern, n),
                      "frac_of_nominal_8tbs": hv["achieved_gbs"] / NOMINAL_HBM_GBS,
                      "kernel_source_sha256_16": kernel_source_hash()},
         "stated_l2_error": accuracy.get(head, {}).get("vs_oracle_64"),

@@ -51,7 +51,9 @@ typedef enum {
     FLAME_ERR_CFL = 2,       /* whistler CFL violated and strict_cfl set (flame_init)   */
     FLAME_ERR_NONFINITE = 3, /* a non-finite density, velocity or field was produced   */
     FLAME_ERR_CUDA = 4,      /* a CUDA runtime or cuFFT call failed                     */
-    FLAME_ERR_STATE = 5      /* state blob or call order inconsistent                   */
+    FLAME_ERR_STATE = 5,     /* state blob or call order inconsistent                   */
+    FLAME_ERR_TIMEOUT = 6    /* a device-side wait (a staged copy of the row kernel)
+                                exceeded its limit; the step was not completed          */
 } flame_status;
 
 typedef enum { FLAME_FP32 = 1, FLAME_FP16 = 2, FLAME_BF16 = 3 } flame_storage;
@@ -86,6 +88,12 @@ typedef struct {
                          (removes launch overhead on small lattices)                    */
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
+    int kernel;       /* 0: automatic -- FLAME_SCHEME with FP16/BF16 storage, 64 <= nx <=
+                         512, nx a multiple of 64 and a 16-byte aligned state uses the
+                         row kernel (x rows staged in shared memory by TMA, two sites
+                         per thread in packed FP32 pairs), everything else the one-site
+                         kernel; 1: always the one-site kernel.  Both compute the same
+                         step in FP32; results agree to FP32 rounding before encoding. */
 } flame_params;
 
 typedef struct {

@@ -61,6 +61,7 @@ flame_status check_params(const flame_params* p) {
   if (p->check_every < 0) return FLAME_ERR_PARAM;
   if (p->graph_steps < 0 || (p->graph_steps & 1)) return FLAME_ERR_PARAM;
   if (p->variant < FLAME_SCHEME || p->variant > FLAME_FD_CURRENT) return FLAME_ERR_PARAM;
+  if (p->kernel < 0 || p->kernel > 1) return FLAME_ERR_PARAM;
   return FLAME_OK;
 }
 
@@ -84,7 +85,10 @@ flame_status sync_and_check(flame_ctx* c) {
   unsigned flag = 0;
   e = cudaMemcpy(&flag, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e);
-  if (flag) {
+  if (flag & 2u) {
+    if (c->sticky == FLAME_OK) c->sticky = FLAME_ERR_TIMEOUT;
+  }
+  if (flag & 1u) {
     c->nonfinite = 1;
     if (c->sticky == FLAME_OK) c->sticky = FLAME_ERR_NONFINITE;
   }
@@ -246,12 +250,15 @@ static cudaError_t capture_graph(flame_ctx* c, int parity) {
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return e;
   cudaGraph_t graph = nullptr;
-  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  // launch configuration (shared-memory opt-in, occupancy) is settled
+  // before capture, so the captured launches call no configuration API
+  e = flame::prepare_step(c->p.storage, c->state, c->g, c->p.variant, c->p.kernel);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < c->p.graph_steps && le == cudaSuccess; ++i)
       le = flame::launch_step(c->p.storage, parity ^ (i & 1), c->state, c->g, c->k, c->d_flags, cs, c->p.variant,
-                              c->d_bfield);
+                              c->d_bfield, c->p.kernel);
     e = cudaStreamEndCapture(cs, &graph);
     if (le != cudaSuccess) e = le;
   }
@@ -285,7 +292,7 @@ flame_status flame_step(flame_ctx* c, int n) {
   }
   for (int i = 0; i < n; ++i) {
     cudaError_t e = flame::launch_step(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream,
-                                       c->p.variant, c->d_bfield);
+                                       c->p.variant, c->d_bfield, c->p.kernel);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->parity ^= 1;
     ++c->step;
@@ -543,6 +550,7 @@ const char* flame_status_string(flame_status s) {
     case FLAME_ERR_NONFINITE: return "non-finite value in the state";
     case FLAME_ERR_CUDA: return "CUDA error";
     case FLAME_ERR_STATE: return "inconsistent state or call order";
+    case FLAME_ERR_TIMEOUT: return "a device-side wait exceeded its limit";
   }
   return "unknown status";
 }

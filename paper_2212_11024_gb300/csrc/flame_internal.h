@@ -29,8 +29,22 @@ constexpr int kVarFdCurrent = 3;  // J from the central-difference curl of B
 
 // storage: 1 FP32, 2 FP16, 3 BF16 (flame_storage).  Bfd: 3 N3 floats of
 // scratch, required by kVarFdCurrent only.
+// kernel: 0 the row kernel where step_row_supported, else the one-site
+// kernel; 1 always the one-site kernel.
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                        cudaStream_t s, int variant = kVarFlame, float* Bfd = nullptr);
+                        cudaStream_t s, int variant = kVarFlame, float* Bfd = nullptr, int kernel = 0);
+
+// The step for 16-bit storage as a persistent kernel over x rows staged in
+// shared memory by TMA, two sites per thread in packed FP32 pairs
+// (step_row.cu): kVarFlame, 64 <= nx <= 512 with nx a multiple of 64, a
+// 16-byte aligned state.  flag bit 1: a non-finite moment; bit 2: a staged
+// copy did not complete within the wait limit.
+bool step_row_supported(Grid g, int storage, int variant, const void* pop);
+// Settles the launch configuration of the kernel launch_step would use
+// (no launch); needed once before stream capture.
+cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel);
+cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
+                            cudaStream_t s);
 
 cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
                         const double* u, const double* B, const double* gu, const double* gB,

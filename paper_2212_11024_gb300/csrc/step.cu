@@ -326,7 +326,9 @@ cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fl
 }  // namespace
 
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                        cudaStream_t s, int variant, float* Bfd) {
+                        cudaStream_t s, int variant, float* Bfd, int kernel) {
+  if (kernel == 0 && step_row_supported(g, storage, variant, pop))
+    return launch_step_row(storage, odd, pop, g, k, flag, s);
   switch (storage) {
     case 1: return step_t<float>(odd, pop, g, k, flag, variant, Bfd, s);
     case 2: return step_t<__half>(odd, pop, g, k, flag, variant, Bfd, s);

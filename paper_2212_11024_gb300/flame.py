@@ -23,9 +23,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libflame.so")
 
-FLAME_OK, FLAME_ERR_PARAM, FLAME_ERR_CFL, FLAME_ERR_NONFINITE, FLAME_ERR_CUDA, FLAME_ERR_STATE = range(6)
+FLAME_OK, FLAME_ERR_PARAM, FLAME_ERR_CFL, FLAME_ERR_NONFINITE, FLAME_ERR_CUDA, FLAME_ERR_STATE, FLAME_ERR_TIMEOUT = range(7)
 STORAGE = {"fp32": 1, "fp16": 2, "bf16": 3}
 VARIANT = {"flame": 0, "bgk": 1, "emhd": 2, "fd_current": 3}
+# flame_params.kernel: "auto" uses the row kernel (TMA-staged rows, packed
+# FP32 pairs) where it applies, "site" always the one-site kernel.
+KERNEL = {"auto": 0, "site": 1}
 NSCALARS = 14
 SCALAR_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "B_x", "B_y", "B_z", "E_u", "E_B", "H_c", "J2", "u_max",
                 "divB_rms", "nonfinite"]
@@ -47,7 +50,7 @@ class Params(ctypes.Structure):
         ("tau_nu", ctypes.c_double), ("tau_eta", ctypes.c_double), ("d_i", ctypes.c_double),
         ("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("B_ref", ctypes.c_double * 3),
         ("init_noneq", ctypes.c_int), ("check_every", ctypes.c_int), ("strict_cfl", ctypes.c_int),
-        ("graph_steps", ctypes.c_int), ("variant", ctypes.c_int),
+        ("graph_steps", ctypes.c_int), ("variant", ctypes.c_int), ("kernel", ctypes.c_int),
     ]
 
 
@@ -112,7 +115,8 @@ def lattice():
 
 
 def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
-                init_noneq=True, check_every=0, strict_cfl=False, graph_steps=0, variant="flame") -> Params:
+                init_noneq=True, check_every=0, strict_cfl=False, graph_steps=0, variant="flame",
+                kernel="auto") -> Params:
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.tau_nu, p.tau_eta, p.d_i = float(tau_nu), float(tau_eta), float(d_i)
@@ -123,6 +127,7 @@ def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_re
     p.init_noneq, p.check_every, p.strict_cfl = int(bool(init_noneq)), int(check_every), int(bool(strict_cfl))
     p.graph_steps = int(graph_steps)
     p.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+    p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
     return p
 
 
@@ -140,7 +145,7 @@ class Flame:
 
     def __init__(self, nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
                  init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None, graph_steps=0,
-                 variant="flame"):
+                 variant="flame", kernel="auto"):
         import torch
 
         if not torch.cuda.is_available():
@@ -149,7 +154,7 @@ class Flame:
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.p = make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage, rho0, B_ref, init_noneq, check_every,
-                             strict_cfl, graph_steps, variant)
+                             strict_cfl, graph_steps, variant, kernel)
         self.shape = (int(nz), int(ny), int(nx))
         self.n3 = int(nx) * int(ny) * int(nz)
         nbytes = state_bytes(self.p)

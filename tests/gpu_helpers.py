@@ -28,12 +28,12 @@ def rel_l2(x, ref):
 
 
 def run_both(shape, tau_nu, tau_eta, d_i, u, B, steps, storage="fp32", rho=None, gradu=None, gradB=None,
-             Bref=(0.0, 0.0, 0.0), literal=True, noneq=True):
+             Bref=(0.0, 0.0, 0.0), literal=True, noneq=True, kernel="auto"):
     """Run the CUDA path and the oracle from the same fields; return
     (gpu populations, gpu moments, oracle populations, oracle moments), all numpy FP64."""
     from paper_2212_11024_gb300 import Flame
     nz, ny, nx = shape
-    sim = Flame(nx, ny, nz, tau_nu, tau_eta, d_i, storage=storage, B_ref=Bref, init_noneq=noneq)
+    sim = Flame(nx, ny, nz, tau_nu, tau_eta, d_i, storage=storage, B_ref=Bref, init_noneq=noneq, kernel=kernel)
     sim.init(rho, u, B, gradu, gradB)
     sim.step(steps)
     sim.sync()

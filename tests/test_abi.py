@@ -45,6 +45,16 @@ def test_lattice_tables_match_app_a(lib):
     assert np.array_equal(xi7, [[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
 
 
+def test_params_struct_matches_header():
+    """The ctypes mirror of flame_params lists the header's fields in order."""
+    from paper_2212_11024_gb300 import flame as F
+    txt = open(os.path.join(ROOT, "include", "flame.h")).read()
+    body = txt[txt.index("typedef struct {", txt.index("flame_variant;")):txt.index("} flame_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b([a-zA-Z_]\w*)\s*(?:\[\d\])?\s*(?=[,;])", body)
+    assert names == [f[0] for f in F.Params._fields_]
+
+
 def test_state_bytes_and_param_validation(lib):
     from paper_2212_11024_gb300 import flame as F
     p = F.make_params(256, 256, 256, 0.51, 0.51, 12.8, "fp32")
@@ -54,15 +64,16 @@ def test_state_bytes_and_param_validation(lib):
     bad = [F.make_params(0, 4, 4, 0.6, 0.6, 0.0), F.make_params(4, 4, 4, 0.5, 0.6, 0.0),
            F.make_params(4, 4, 4, 0.6, 0.4, 0.0), F.make_params(4, 4, 4, 0.6, 0.6, -1.0),
            F.make_params(4, 4, 4, 0.6, 0.6, 0.0, storage=7), F.make_params(2048, 1024, 1024, 0.6, 0.6, 0.0),
-           F.make_params(4, 4, 4, 0.6, 0.6, float("nan")), F.make_params(4, 4, 4, 0.6, 0.6, 0.0, rho0=0.0)]
+           F.make_params(4, 4, 4, 0.6, 0.6, float("nan")), F.make_params(4, 4, 4, 0.6, 0.6, 0.0, rho0=0.0),
+           F.make_params(4, 4, 4, 0.6, 0.6, 0.0, kernel=2)]
     for b in bad:
         assert F.state_bytes(b) == 0
 
 
 def test_status_strings(lib):
     lib.flame_status_string.restype = ctypes.c_char_p
-    texts = {lib.flame_status_string(i).decode() for i in range(6)}
-    assert len(texts) == 6 and "ok" in texts
+    texts = {lib.flame_status_string(i).decode() for i in range(7)}
+    assert len(texts) == 7 and "ok" in texts
 
 
 def test_flame_create_rejects_bad_arguments_without_touching_the_gpu(lib):

@@ -1,0 +1,78 @@
+"""The row kernel for 16-bit storage (x rows staged in shared memory by TMA,
+two sites per thread in packed FP32 pairs) against the FP64 oracle and
+against the one-site kernel.  Row lengths 64, 128 and 512 take the
+compile-time row length instantiations, 192 the general one."""
+import numpy as np
+import pytest
+
+from gpu_helpers import rel_l2, run_both, turbulence
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(6, 5, 64), (4, 3, 128), (3, 4, 192), (2, 3, 512)]
+B0 = np.array([0.0, 0.02, 0.05])
+
+
+def _fields(shape, seed):
+    u, B = turbulence(shape, seed, 0.05, shells=(1, 2))
+    return u, B + B0[:, None, None, None]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-2), ("bf16", 1e-1)])
+def test_row_kernel_vs_oracle(shape, storage, tol):
+    """21 steps (ending on an odd-parity state) of Hall turbulence with a mean
+    field, per-field relative L2 of the fluctuations against the FP64 oracle;
+    density to 1e-3."""
+    u, B = _fields(shape, 41)
+    fg, mg, fo, mo = run_both(shape, 0.52, 0.55, 1.5, u, B, 21, storage=storage, literal=False, Bref=tuple(B0))
+    b0 = B0[:, None, None, None]
+    assert rel_l2(mg["u"], mo["u"]) < tol
+    assert rel_l2(mg["B"] - b0, mo["B"] - b0) < tol
+    assert rel_l2(mg["J"], mo["J"]) < tol
+    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-3
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("storage,ulps", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_row_kernel_agrees_with_site_kernel(shape, storage, ulps):
+    """Same fields, 9 steps, kernel "auto" (row kernel) vs "site": both compute
+    the collision in FP32 in a different order, so the stored deviations
+    differ by a few units of the storage's last place at some entries -- and
+    do differ somewhere, which shows that the row kernel ran."""
+    from paper_2212_11024_gb300 import Flame
+    nz, ny, nx = shape
+    u, B = _fields(shape, 43)
+    pops = []
+    for kernel in ("auto", "site"):
+        sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), kernel=kernel)
+        sim.init(None, u, B)
+        sim.step(9)
+        pops.append(sim.populations().cpu().numpy())
+        sim.close()
+    a, b = pops
+    dev = np.abs(b - np.median(b, axis=(1, 2, 3), keepdims=True)).max()
+    d = np.abs(a - b)
+    assert d.max() < 8 * ulps * dev, d.max() / dev
+    assert (d > 0).any()
+    assert (d > 0).mean() < 0.5
+
+
+def test_row_kernel_graph_replay_is_bit_identical():
+    """graph_steps replays of the row kernel equal single launches."""
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    shape = (4, 3, 128)
+    nz, ny, nx = shape
+    u, B = _fields(shape, 45)
+    a = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0))
+    b = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0), graph_steps=8)
+    for s in (a, b):
+        s.init(None, u, B)
+    for n in (3, 37, 20):
+        a.step(n)
+        b.step(n)
+    assert torch.equal(a.populations(), b.populations())
+    assert a.sync() is None and b.sync() is None
+    a.close()
+    b.close()
