@@ -27,14 +27,22 @@
  *    N3 = nx*ny*nz sites per component.  Gradients are [3a+b][z][y][x] for
  *    d_a F_b.
  *
- * Population state (flame_state_bytes bytes, 256-byte aligned): 48 slots of
- * N3 values.  Slot q = 0..26 holds the fluid population on App. A's D3Q27
- * velocity q; slot 27 + 7b + i the magnetic component b (x, y, z) on D3Q7
- * velocity i (rest, +x, -x, +y, -y, +z, -z).  The state is updated in place
- * with the AA access pattern, so which site and slot hold a given population
- * depends on the step parity (flame_info).  A slot stores the population's
- * deviation from the rest equilibrium of the reference state (rho0, B_ref)
- * divided by its lattice weight, as FP32, FP16 or BF16 (round to nearest even).
+ * Populations are numbered in natural slot order: q = 0..26 the fluid
+ * population on App. A's D3Q27 velocity q, q = 27 + 7b + i the magnetic
+ * component b (x, y, z) on D3Q7 velocity i (rest, +x, -x, +y, -y, +z, -z).
+ * flame_populations and the adjoint vectors use this order.
+ *
+ * Population state (flame_state_bytes bytes, 256-byte aligned; opaque to
+ * callers, who move it only with flame_get_state / flame_set_state): 48
+ * storage slots of N3 values.  Storage slot (cx+1) + 3(cy+1) + 9(cz+1) holds
+ * the fluid population on velocity (cx, cy, cz), storage slot 27 + 3i + b
+ * the magnetic component b on D3Q7 velocity i; this order makes the rows an
+ * odd AA step reads into a few runs of consecutive slots.  The state is
+ * updated in place with the AA access pattern, so which site and slot hold a
+ * given population depends on the step parity (flame_info).  A slot stores
+ * the population's deviation from the rest equilibrium of the reference
+ * state (rho0, B_ref) divided by its lattice weight, as FP32, FP16 or BF16
+ * (round to nearest even).
  */
 #ifndef FLAME_H
 #define FLAME_H
@@ -178,7 +186,7 @@ flame_status flame_moments(flame_ctx *ctx, double *d_rho, double *d_u, double *d
 flame_status flame_probe(flame_ctx *ctx, int nsites, const long long *d_sites, double *d_out);
 
 /* The current pre-collision populations decoded to FP64 in natural order,
- * d_f [48][N3] with the slot numbering above, whatever the AA parity.
+ * d_f [48][N3] in natural slot order, whatever the AA parity.
  * Asynchronous. */
 flame_status flame_populations(flame_ctx *ctx, double *d_f);
 

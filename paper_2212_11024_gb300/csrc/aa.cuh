@@ -35,31 +35,39 @@ __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const Grid& g) {
 //   even: same site, opposite slot;    odd: site + c, own slot.
 template <bool ODD>
 __device__ __forceinline__ long long src27(int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)opp27(i) * n3 + site + nb(-cx27(i), -cy27(i), -cz27(i))
-             : (long long)i * n3 + site;
+  return ODD ? (long long)phys(opp27(i)) * n3 + site + nb(-cx27(i), -cy27(i), -cz27(i))
+             : (long long)phys(i) * n3 + site;
 }
 template <bool ODD>
 __device__ __forceinline__ long long dst27(int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))
-             : (long long)opp27(i) * n3 + site;
+  return ODD ? (long long)phys(i) * n3 + site + nb(cx27(i), cy27(i), cz27(i))
+             : (long long)phys(opp27(i)) * n3 + site;
 }
 template <bool ODD>
 __device__ __forceinline__ long long src7(int b, int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)mslot(b, opp7(i)) * n3 + site + nb(-mx7(i), -my7(i), -mz7(i))
-             : (long long)mslot(b, i) * n3 + site;
+  return ODD ? (long long)phys(mslot(b, opp7(i))) * n3 + site + nb(-mx7(i), -my7(i), -mz7(i))
+             : (long long)phys(mslot(b, i)) * n3 + site;
 }
 template <bool ODD>
 __device__ __forceinline__ long long dst7(int b, int i, int site, const Nbr& nb, long long n3) {
-  return ODD ? (long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))
-             : (long long)mslot(b, opp7(i)) * n3 + site;
+  return ODD ? (long long)phys(mslot(b, i)) * n3 + site + nb(mx7(i), my7(i), mz7(i))
+             : (long long)phys(mslot(b, opp7(i))) * n3 + site;
 }
 
-// Base pointers of the 48 slots (slot q starts at q * N3), passed as kernel
-// parameters so that each access is one index computation on a parameter.
+// Base pointers of the 48 populations in natural slot order (natural slot
+// q starts at phys(q) * N3), passed as kernel parameters so that each access
+// is one index computation on a parameter.
 template <class T>
 struct Slots {
   T* p[kPop];
 };
+template <class T>
+inline Slots<T> make_slots(const void* pop, const Grid& g) {
+  Slots<T> P;
+  for (int q = 0; q < kPop; ++q)
+    P.p[q] = const_cast<T*>(static_cast<const T*>(pop)) + (size_t)phys(q) * (size_t)g.n3;
+  return P;
+}
 
 // Site offset of the source (pre-collision) and destination
 // (post-collision) of the population on velocity (cx, cy, cz), and the

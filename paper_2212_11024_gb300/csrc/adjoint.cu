@@ -505,8 +505,7 @@ template <class T>
 cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, const float* lin, float* lout,
                       double* partials, long long nblk, double* ddi, cudaStream_t s) {
   const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
-  Slots<T> P;
-  for (int q = 0; q < kPop; ++q) P.p[q] = const_cast<T*>(static_cast<const T*>(pop)) + (size_t)q * (size_t)g.n3;
+  const Slots<T> P = make_slots<T>(pop, g);
   if (odd)
     adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, lin, lout, partials);
   else

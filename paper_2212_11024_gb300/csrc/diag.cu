@@ -79,7 +79,7 @@ __global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq
     const double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
     const double L = 4.5 * (miso * (c2 - 1.0) - cNc + trN3);
     const double ne = 4.5 * (cPc - trPn3);
-    pop[(long long)i * n3 + site] = Codec<T>::enc((float)(drho + rho * E + L + ne));
+    pop[(long long)phys(i) * n3 + site] = Codec<T>::enc((float)(drho + rho * E + L + ne));
   }
   const double V[3] = {U[0] - aH * J0[0], U[1] - aH * J0[1], U[2] - aH * J0[2]};
   for (int bb = 0; bb < 3; ++bb)
@@ -91,7 +91,7 @@ __global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq
         ne += xi[a] * dB[3 * a + bb];
       }
       const double v = b[bb] + 4.0 * l0 - (noneq ? ne / omegaB : 0.0);
-      pop[(long long)mslot(bb, i) * n3 + site] = Codec<T>::enc((float)v);
+      pop[(long long)phys(mslot(bb, i)) * n3 + site] = Codec<T>::enc((float)v);
     }
   const double va = sqrt((B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho);
   const double um = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);

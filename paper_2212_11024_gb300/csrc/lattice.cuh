@@ -51,8 +51,26 @@ __host__ __device__ constexpr int mz7(int i) { return i == 5 ? 1 : (i == 6 ? -1 
 __host__ __device__ constexpr int opp27(int i) { return i == 0 ? 0 : (i <= 13 ? i + 13 : i - 13); }
 __host__ __device__ constexpr int opp7(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
-// Slot of a population in the 48-slot state: fluid q, magnetic 27 + 7b + i.
+// Natural slot of a population: fluid q (App. A order), magnetic 27 + 7b + i.
 __host__ __device__ constexpr int mslot(int b, int i) { return kQ + kM * b + i; }
+
+// Storage slot of natural slot q in the state: fluid populations in
+// velocity-cube order (cx+1) + 3(cy+1) + 9(cz+1), magnetic ones
+// velocity-major 27 + 3i + b.  Then the 48 rows an odd AA step reads for an
+// x row form 16 runs of 3 consecutive storage slots, each run from a single
+// (y, z) row: the fluid run of (cy, cz) and the magnetic run of velocity i.
+__host__ __device__ constexpr int phys(int q) {
+  return q < kQ ? (cx27(q) + 1) + 3 * (cy27(q) + 1) + 9 * (cz27(q) + 1) : kQ + 3 * ((q - kQ) % kM) + (q - kQ) / kM;
+}
+constexpr bool phys_is_permutation() {
+  for (int a = 0; a < kPop; ++a) {
+    if (phys(a) < 0 || phys(a) >= kPop) return false;
+    for (int b = a + 1; b < kPop; ++b)
+      if (phys(a) == phys(b)) return false;
+  }
+  return true;
+}
+static_assert(phys_is_permutation(), "storage slots must be a permutation of the natural slots");
 
 // Sec. 3.1.1 weights by |c|^2 (8/27, 2/27, 1/54, 1/216); they factor into
 // the 1-D weights 2/3 (c = 0) and 1/6 (c = +-1).

@@ -301,8 +301,7 @@ template <class T>
 cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, int variant, float* Bfd,
                    cudaStream_t s) {
   const dim3 b = site_block(g, kStepThreads), gr = site_grid(g, b);
-  Slots<T> P;
-  for (int q = 0; q < kPop; ++q) P.p[q] = static_cast<T*>(pop) + (size_t)q * (size_t)g.n3;
+  const Slots<T> P = make_slots<T>(pop, g);
   switch (variant) {
     case kVarFlame: step_launch<T, kVarFlame>(odd, P, g, k, flag, nullptr, gr, b, s); break;
     case kVarBgkFluid: step_launch<T, kVarBgkFluid>(odd, P, g, k, flag, nullptr, gr, b, s); break;

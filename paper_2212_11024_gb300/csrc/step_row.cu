@@ -8,10 +8,11 @@
 // encode and AA store) are those of the one-site kernel in step.cu, and so
 // is the layout of the state.  What differs is the data movement:
 //  - For each tile (one x row (y, z)) warp 0 stages the 48 source rows of
-//    the AA pattern in shared memory with TMA bulk copies completed on an
-//    mbarrier: the row (y, z) of every slot on even steps, the row
-//    (y, z) - (c_y, c_z) of the opposite slot on odd steps.  Two stages: the
-//    copies of the next tile overlap the arithmetic of this one.
+//    the AA pattern in shared memory with TMA copies completed on an
+//    mbarrier: the row (y, z) of every slot on even steps (one tensor-map
+//    box), the row (y, z) - (c_y, c_z) of the opposite slot on odd steps
+//    (16 boxes of three consecutive storage slots, see phys()).  Two stages:
+//    the copies of the next tile overlap the arithmetic of this one.
 //  - The x shift of the odd step becomes a wrap-around index into the
 //    staged row.  Thread t takes the sites (2t, 2t + 1); unshifted values
 //    are read from shared memory, and stored to HBM, as one 32-bit pair.
@@ -19,7 +20,11 @@
 //    which is what limited the one-site kernel with 16-bit storage.
 // Requirements: 16-bit storage, the paper's scheme, 64 <= nx <= 512 with nx
 // a multiple of 64 (row copies of whole 16-byte units, a whole number of
-// warps), a 16-byte aligned state.
+// warps), a 16-byte aligned state.  Rows longer than 256 sites are staged by
+// one bulk copy per storage slot instead of tensor-map boxes.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
 
 #include "aa.cuh"
@@ -271,15 +276,19 @@ __device__ __forceinline__ void collide_pair(const LdF& ldf, const LdG& ldg, con
 constexpr int kRowStages = 2;
 constexpr int kRowMaxThreads = 256;
 constexpr int kRowMinBlocks = 2;
+// Rows up to this length are staged by tensor-map copies (a box is at most
+// 256 elements wide), longer ones by one bulk copy per row.
+constexpr int kBoxMaxX = 256;
 // mbarrier.try_wait returns after a bounded, hardware-defined time; this
 // many tries (far longer than any copy takes) end the wait with an error.
 constexpr unsigned kWaitTries = 1u << 22;
 
-// Source of staged row q (fluid: q = px + 3 py + 9 pz; magnetic: 27 + 7 c + i):
-// the slot and the row offset (dy, dz) added to the row's (y, z).
-struct RowPlan {
-  signed char slot[kPop], dy[kPop], dz[kPop];
-};
+// Storage slots come in 16 runs of three (see phys()).  On an odd step run r
+// is staged from the row (y, z) + (dy, dz): the fluid run r = (cy+1) + 3(cz+1)
+// from (cy, cz), the magnetic run 9 + i from the D3Q7 velocity i.
+constexpr int kRuns = 16;
+__host__ __device__ constexpr int run_dy(int r) { return r < 9 ? r % 3 - 1 : my7(r - 9); }
+__host__ __device__ constexpr int run_dz(int r) { return r < 9 ? r / 3 - 1 : mz7(r - 9); }
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -312,55 +321,59 @@ __device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigne
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// Tensor-map copy of the box at (x, y, z, slot) of the state viewed as
+// [48][nz][ny][nx], completing bytes on the mbarrier.
+__device__ __forceinline__ void tensor_load(unsigned dst, const CUtensorMap* map, int y, int z, int slot, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(z), "r"(slot), "r"(bar)
+      : "memory");
+}
 
-// Row geometry.  NX > 0 fixes the row length at compile time (shared-memory
-// offsets become immediates); NX = 0 reads it from the grid.
-template <class T, int NX>
-struct Rows {
-  int nx, ny, nz;
-  unsigned rowbytes;
-  __device__ __forceinline__ explicit Rows(const Grid& g)
-      : nx(NX ? NX : g.nx), ny(g.ny), nz(g.nz), rowbytes(static_cast<unsigned>(NX ? NX : g.nx) * sizeof(T)) {}
-  // global row that staged row q of a tile is a copy of
-  __device__ __forceinline__ const T* src(const Slots<T>& P, const RowPlan& plan, int tile, int q) const {
-    int ys = tile % ny + plan.dy[q], zs = tile / ny + plan.dz[q];
-    ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-    zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-    return P.p[plan.slot[q]] + ((long long)zs * ny + ys) * nx;
-  }
-};
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// The site pair (2t, 2t + 1) of a staged tile: ld(q, d) reads staged row q
-// at the pair moved by d sites (d = -c_x reads velocity c on an odd step;
-// d = 0 on even steps).
+// The site pair (2t, 2t + 1) of a staged tile: ld(s, d) reads staged
+// storage slot s at the pair moved by d sites (d = -c_x reads velocity c on
+// an odd step; d = 0 on even steps).  NX > 0 fixes the row length at compile
+// time (shared-memory offsets become immediates); NX = 0 reads it from the
+// grid.
 template <class T, bool ODD, int NX>
 struct PairAccess {
-  T* R;
+  const T* R;
   int nx, x0, x1, xm0, xp1;
-  __device__ __forceinline__ PairAccess(T* rows, int n) : R(rows), nx(NX ? NX : n) {
+  __device__ __forceinline__ PairAccess(const T* rows, int n) : R(rows), nx(NX ? NX : n) {
     x0 = 2 * threadIdx.x;
     x1 = x0 + 1;
     xm0 = x0 == 0 ? nx - 1 : x0 - 1;
     xp1 = x1 == nx - 1 ? 0 : x1 + 1;
   }
-  __device__ __forceinline__ f2 ld(int q, int d) const {
-    const T* r = R + q * nx;
+  __device__ __forceinline__ f2 ld(int s, int d) const {
+    const T* r = R + s * nx;
     if (!ODD || d == 0) return Codec2<T>::dec(r + x0);
     if (d < 0) return pack(Codec<T>::dec(r[xm0]), Codec<T>::dec(r[x0]));
     return pack(Codec<T>::dec(r[x1]), Codec<T>::dec(r[xp1]));
   }
 };
 
+// Tensor maps of the state as [48][nz][ny][nx]: one box of a row of all 48
+// slots (even steps) and one of a row of 3 consecutive slots (odd steps).
+struct RowMaps {
+  CUtensorMap all, run;
+};
+
 template <class T, bool ODD, int NX>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
-    step_row_kernel(Slots<T> P, RowPlan plan, Grid g, StepConsts k, unsigned* __restrict__ flag) {
+    step_row_kernel(Slots<T> P, const T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
+                    const __grid_constant__ RowMaps maps) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const Rows<T, NX> geo(g);
-  const int nx = geo.nx, ny = geo.ny, nz = geo.nz;
-  T* rows = reinterpret_cast<T*>(smem);  // [stage][48][nx]
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kRowStages * kPop * geo.rowbytes);
+  const int nx = NX ? NX : g.nx, ny = g.ny, nz = g.nz;
+  const unsigned rowbytes = static_cast<unsigned>(nx) * sizeof(T);
+  T* rows = reinterpret_cast<T*>(smem);  // [stage][48 storage slots][nx]
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kRowStages * kPop * rowbytes);
   const int ntiles = ny * nz;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool boxed = nx <= kBoxMaxX;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRowStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
@@ -368,12 +381,27 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
   }
   __syncthreads();
 
-  auto issue = [&](int tile, int st) {  // warp 0
+  // Warp 0 stages the 48 source rows of tile (y, z) into stage st.
+  auto issue = [&](int tile, int st) {
+    const int y = tile % ny, z = tile / ny;
     const unsigned bar = smem_addr(&bars[st]);
-    if (lane == 0) mbar_expect_tx(bar, kPop * geo.rowbytes);
+    T* dst = rows + (size_t)st * kPop * nx;
+    if (lane == 0) mbar_expect_tx(bar, kPop * rowbytes);
     __syncwarp();
-    for (int q = lane; q < kPop; q += 32)
-      bulk_load(smem_addr(rows + ((size_t)st * kPop + q) * nx), geo.src(P, plan, tile, q), geo.rowbytes, bar);
+    if (boxed) {
+      if (!ODD) {
+        if (lane == 0) tensor_load(smem_addr(dst), &maps.all, y, z, 0, bar);
+      } else if (lane < kRuns) {
+        tensor_load(smem_addr(dst + 3 * lane * nx), &maps.run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz),
+                    3 * lane, bar);
+      }
+    } else {
+      for (int s = lane; s < kPop; s += 32) {
+        const int r = s / 3;
+        const int ys = ODD ? wrap(y + run_dy(r), ny) : y, zs = ODD ? wrap(z + run_dz(r), nz) : z;
+        bulk_load(smem_addr(dst + s * nx), state + (size_t)s * g.n3 + ((long long)zs * ny + ys) * nx, rowbytes, bar);
+      }
+    }
   };
 
   const int first = blockIdx.x, stride = gridDim.x;
@@ -388,14 +416,9 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
     if (ok) {
       const int y = tile % ny, z = tile / ny;
       const PairAccess<T, ODD, NX> A(rows + (size_t)st * kPop * nx, nx);
-      auto row_of = [&](int cy, int cz) {
-        int ys = y + cy, zs = z + cz;
-        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-        return ((long long)zs * ny + ys) * nx;
-      };
-      // post-collision pair of velocity c into slot `slot`: even steps the
-      // site pair itself, odd steps the pair moved by c.
+      auto row_of = [&](int cy, int cz) { return ((long long)wrap(z + cz, nz) * ny + wrap(y + cy, ny)) * nx; };
+      // post-collision pair of velocity c into natural slot `slot`: even
+      // steps the site pair itself, odd steps the pair moved by c.
       auto st2 = [&](int slot, int cx, int cy, int cz, f2 v) {
         T* b = P.p[slot] + (ODD ? row_of(cy, cz) : row_of(0, 0));
         if (!ODD || cx == 0) {
@@ -408,8 +431,13 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
           b[A.x0] = Codec<T>::enc(v.v.y);
         }
       };
-      auto ldf = [&](int px, int py, int pz) { return A.ld(px + 3 * py + 9 * pz, 1 - px); };
-      auto ldg = [&](int c, int i) { return A.ld(kQ + kM * c + i, -mx7(i)); };
+      // staged storage slot of velocity (px, py, pz): its own on even steps,
+      // that of the opposite velocity on odd steps (26 - cube index)
+      auto ldf = [&](int px, int py, int pz) {
+        const int q = px + 3 * py + 9 * pz;
+        return A.ld(ODD ? 26 - q : q, 1 - px);
+      };
+      auto ldg = [&](int c, int i) { return A.ld(kQ + 3 * (ODD ? opp7(i) : i) + c, -mx7(i)); };
       auto stf = [&](int px, int py, int pz, f2 v) {
         const int i = idx27(px, py, pz);
         st2(ODD ? i : opp27(i), px - 1, py - 1, pz - 1, v);
@@ -428,33 +456,6 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
     }
     if (warp == 0 && tile + kRowStages * stride < ntiles) issue(tile + kRowStages * stride, st);
   }
-}
-
-RowPlan make_plan(bool odd) {
-  RowPlan p;
-  for (int pz = 0; pz < 3; ++pz)
-    for (int py = 0; py < 3; ++py)
-      for (int px = 0; px < 3; ++px) {
-        const int q = px + 3 * py + 9 * pz, i = idx27(px, py, pz);
-        p.slot[q] = (signed char)(odd ? opp27(i) : i);
-        p.dy[q] = (signed char)(odd ? 1 - py : 0);
-        p.dz[q] = (signed char)(odd ? 1 - pz : 0);
-      }
-  for (int c = 0; c < 3; ++c)
-    for (int i = 0; i < kM; ++i) {
-      const int q = kQ + kM * c + i;
-      p.slot[q] = (signed char)mslot(c, odd ? opp7(i) : i);
-      p.dy[q] = (signed char)(odd ? -my7(i) : 0);
-      p.dz[q] = (signed char)(odd ? -mz7(i) : 0);
-    }
-  return p;
-}
-
-template <class T>
-Slots<T> slots_of(void* pop, const Grid& g) {
-  Slots<T> P;
-  for (int q = 0; q < kPop; ++q) P.p[q] = static_cast<T*>(pop) + (size_t)q * (size_t)g.n3;
-  return P;
 }
 
 size_t row_smem_bytes(int nx, size_t elem) { return kRowStages * (kPop * (size_t)nx * elem + sizeof(unsigned long long)); }
@@ -489,13 +490,53 @@ cudaError_t row_config(const Grid& g, int* grid, size_t* smem_out) {
   return cudaSuccess;
 }
 
+// Tensor maps of a state (16-bit values), cached for the last state seen by
+// this thread.  The encoder comes from the driver through the runtime, so the
+// library links no driver library.
+cudaError_t row_maps(const void* pop, const Grid& g, RowMaps* out) {
+  thread_local const void* last_pop = nullptr;
+  thread_local Grid last_g{};
+  thread_local RowMaps last{};
+  if (pop == last_pop && g.nx == last_g.nx && g.ny == last_g.ny && g.nz == last_g.nz) {
+    *out = last;
+    return cudaSuccess;
+  }
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)kPop};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 2, (cuuint64_t)g.nx * g.ny * 2, (cuuint64_t)g.n3 * 2};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  RowMaps m;
+  for (int w = 0; w < 2; ++w) {
+    const cuuint32_t box[4] = {(cuuint32_t)g.nx, 1, 1, w == 0 ? (cuuint32_t)kPop : 3u};
+    CUresult r = encode(w == 0 ? &m.all : &m.run, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(pop), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  last_pop = pop;
+  last_g = g;
+  last = m;
+  *out = m;
+  return cudaSuccess;
+}
+
 template <class T, bool ODD, int NX>
 cudaError_t row_launch(void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch) {
   int grid = 0;
   size_t smem = 0;
   cudaError_t e = row_config<T, ODD, NX>(g, &grid, &smem);
+  RowMaps maps{};
+  if (e == cudaSuccess && g.nx <= kBoxMaxX) e = row_maps(pop, g, &maps);
   if (e != cudaSuccess || !launch) return e;
-  step_row_kernel<T, ODD, NX><<<grid, g.nx / 2, smem, s>>>(slots_of<T>(pop, g), make_plan(ODD), g, k, flag);
+  step_row_kernel<T, ODD, NX><<<grid, g.nx / 2, smem, s>>>(make_slots<T>(pop, g), static_cast<const T*>(pop), g, k,
+                                                            flag, maps);
   return cudaGetLastError();
 }
 
