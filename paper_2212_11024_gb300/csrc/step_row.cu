@@ -15,12 +15,15 @@
 //    the copies of the next tile overlap the arithmetic of this one.
 //  - The x shift of the odd step becomes a wrap-around index into the
 //    staged row.  Thread t takes the sites (2t, 2t + 1); unshifted values
-//    are read from shared memory, and stored to HBM, as one 32-bit pair.
+//    are read and written as one 32-bit pair.
+//  - The collision writes its results in place into the staged rows (under
+//    the AA pattern each result lands where the same thread read), and warp
+//    0 writes the tile back with TMA stores to the rows it was loaded from.
 //  - The packed arithmetic halves the FP32 instruction count per site,
 //    which is what limited the one-site kernel with 16-bit storage.
 // Requirements: 16-bit storage, the paper's scheme, 64 <= nx <= 512 with nx
 // a multiple of 64 (row copies of whole 16-byte units, a whole number of
-// warps), a 16-byte aligned state.  Rows longer than 256 sites are staged by
+// warps), a 16-byte aligned state.  Rows longer than 256 sites are moved by
 // one bulk copy per storage slot instead of tensor-map boxes.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -269,11 +272,9 @@ __device__ __forceinline__ void collide_pair(const LdF& ldf, const LdG& ldg, con
 }
 
 // ------------------------------------------- rows staged by TMA, persistent
-// Two stages (the copies of the next row overlap the arithmetic of this
-// one), at most 256 threads (nx <= 512) and 128 registers per thread (two
-// 256-thread blocks per SM).  Chosen by timing at 256^3: three stages, or
-// 210 registers, leave fewer warps per SM and run slower.
-constexpr int kRowStages = 2;
+// At most 256 threads (nx <= 512) and 128 registers per thread (two
+// 256-thread blocks per SM; 210 registers, the unconstrained allocation,
+// leave fewer warps and ran slower at 256^3).  Stages: row_stages().
 constexpr int kRowMaxThreads = 256;
 constexpr int kRowMinBlocks = 2;
 // Rows up to this length are staged by tensor-map copies (a box is at most
@@ -331,11 +332,29 @@ __device__ __forceinline__ void tensor_load(unsigned dst, const CUtensorMap* map
       : "memory");
 }
 
+// ... and back: shared -> global, in the bulk async-group of the thread.
+__device__ __forceinline__ void tensor_store(const CUtensorMap* map, int y, int z, int slot, unsigned src) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(0), "r"(y), "r"(z), "r"(slot), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, unsigned src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the thread's committed stores have read their shared-memory source / are complete
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_done() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's shared-memory writes before later TMA reads of them
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // The site pair (2t, 2t + 1) of a staged tile: ld(s, d) reads staged
 // storage slot s at the pair moved by d sites (d = -c_x reads velocity c on
-// an odd step; d = 0 on even steps).  NX > 0 fixes the row length at compile
+// an odd step; d = 0 on even steps), st(s, d, v) writes it there.  NX > 0 fixes the row length at compile
 // time (shared-memory offsets become immediates); NX = 0 reads it from the
 // grid.
 template <class T, bool ODD, int NX>
@@ -354,6 +373,18 @@ struct PairAccess {
     if (d < 0) return pack(Codec<T>::dec(r[xm0]), Codec<T>::dec(r[x0]));
     return pack(Codec<T>::dec(r[x1]), Codec<T>::dec(r[xp1]));
   }
+  __device__ __forceinline__ void st(int s, int d, f2 v) const {
+    T* r = const_cast<T*>(R) + s * nx;
+    if (!ODD || d == 0) {
+      Codec2<T>::enc(r + x0, v);
+    } else if (d < 0) {
+      r[xm0] = Codec<T>::enc(v.v.x);
+      r[x0] = Codec<T>::enc(v.v.y);
+    } else {
+      r[x1] = Codec<T>::enc(v.v.x);
+      r[xp1] = Codec<T>::enc(v.v.y);
+    }
+  }
 };
 
 // Tensor maps of the state as [48][nz][ny][nx]: one box of a row of all 48
@@ -362,9 +393,9 @@ struct RowMaps {
   CUtensorMap all, run;
 };
 
-template <class T, bool ODD, int NX>
+template <class T, bool ODD, int NX, int kRowStages>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
-    step_row_kernel(Slots<T> P, const T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
+    step_row_kernel(T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
                     const __grid_constant__ RowMaps maps) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nx = NX ? NX : g.nx, ny = g.ny, nz = g.nz;
@@ -381,7 +412,10 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
   }
   __syncthreads();
 
-  // Warp 0 stages the 48 source rows of tile (y, z) into stage st.
+  // Warp 0 moves the 48 rows of tile (y, z) between HBM and stage st: the
+  // rows (y, z) of all storage slots on even steps, run r of three storage
+  // slots from the row (y, z) + (run_dy(r), run_dz(r)) on odd steps.  The
+  // store writes each row back to where it was loaded from.
   auto issue = [&](int tile, int st) {
     const int y = tile % ny, z = tile / ny;
     const unsigned bar = smem_addr(&bars[st]);
@@ -403,10 +437,38 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
       }
     }
   };
+  auto store = [&](int tile, int st) {  // returns once the stage has been read
+    const int y = tile % ny, z = tile / ny;
+    const T* src = rows + (size_t)st * kPop * nx;
+    if (boxed) {
+      if (!ODD) {
+        if (lane == 0) tensor_store(&maps.all, y, z, 0, smem_addr(src));
+      } else if (lane < kRuns) {
+        tensor_store(&maps.run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz), 3 * lane,
+                     smem_addr(src + 3 * lane * nx));
+      }
+    } else {
+      for (int s = lane; s < kPop; s += 32) {
+        const int r = s / 3;
+        const int ys = ODD ? wrap(y + run_dy(r), ny) : y, zs = ODD ? wrap(z + run_dz(r), nz) : z;
+        bulk_store(state + (size_t)s * g.n3 + ((long long)zs * ny + ys) * nx, smem_addr(src + s * nx), rowbytes);
+      }
+    }
+    bulk_commit();
+    // Two stages: this stage is refilled next, so its rows must have been
+    // read out.  Three: the stage refilled next held the previous tile,
+    // whose store is the older of the two groups in flight.
+    if (kRowStages == 2) bulk_wait_read();
+    else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    __syncwarp();
+  };
 
   const int first = blockIdx.x, stride = gridDim.x;
+  // Tiles staged before the loop: both stages with two; with three, two of
+  // them (the third is filled once the first tile's store has drained).
+  constexpr int kAhead = kRowStages == 2 ? 2 : kRowStages - 1;
   if (warp == 0)
-    for (int s = 0; s < kRowStages; ++s)
+    for (int s = 0; s < kAhead; ++s)
       if (first + s * stride < ntiles) issue(first + s * stride, s);
 
   int it = 0;
@@ -414,59 +476,68 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
     const int st = it % kRowStages;
     const bool ok = mbar_wait(smem_addr(&bars[st]), (it / kRowStages) & 1);
     if (ok) {
-      const int y = tile % ny, z = tile / ny;
+      // Collide in place.  The post-collision value of velocity c belongs in
+      // the staged slot of the opposite velocity (on odd steps: the slot of
+      // c itself, staged from the row (y, z) + (c_y, c_z)) at the position
+      // this pair read that slot from, so each thread writes only what it
+      // has read, and every staged row is the new content of the HBM row it
+      // was loaded from.
       const PairAccess<T, ODD, NX> A(rows + (size_t)st * kPop * nx, nx);
-      auto row_of = [&](int cy, int cz) { return ((long long)wrap(z + cz, nz) * ny + wrap(y + cy, ny)) * nx; };
-      // post-collision pair of velocity c into natural slot `slot`: even
-      // steps the site pair itself, odd steps the pair moved by c.
-      auto st2 = [&](int slot, int cx, int cy, int cz, f2 v) {
-        T* b = P.p[slot] + (ODD ? row_of(cy, cz) : row_of(0, 0));
-        if (!ODD || cx == 0) {
-          Codec2<T>::enc(b + A.x0, v);
-        } else if (cx > 0) {
-          b[A.x1] = Codec<T>::enc(v.v.x);
-          b[A.xp1] = Codec<T>::enc(v.v.y);
-        } else {
-          b[A.xm0] = Codec<T>::enc(v.v.x);
-          b[A.x0] = Codec<T>::enc(v.v.y);
-        }
-      };
-      // staged storage slot of velocity (px, py, pz): its own on even steps,
-      // that of the opposite velocity on odd steps (26 - cube index)
       auto ldf = [&](int px, int py, int pz) {
         const int q = px + 3 * py + 9 * pz;
         return A.ld(ODD ? 26 - q : q, 1 - px);
       };
       auto ldg = [&](int c, int i) { return A.ld(kQ + 3 * (ODD ? opp7(i) : i) + c, -mx7(i)); };
       auto stf = [&](int px, int py, int pz, f2 v) {
-        const int i = idx27(px, py, pz);
-        st2(ODD ? i : opp27(i), px - 1, py - 1, pz - 1, v);
+        const int q = px + 3 * py + 9 * pz;
+        A.st(ODD ? q : 26 - q, px - 1, v);
       };
-      auto stg = [&](int c, int i, f2 v) { st2(mslot(c, ODD ? i : opp7(i)), mx7(i), my7(i), mz7(i), v); };
+      auto stg = [&](int c, int i, f2 v) { A.st(kQ + 3 * (ODD ? i : opp7(i)) + c, mx7(i), v); };
       collide_pair(ldf, ldg, stf, stg, k, flag);
+      fence_proxy_async();
     }
     // Every thread is done with this stage before it is refilled.
     if (__syncthreads_or(!ok)) {
       // A copy did not complete in time: report it, let the copies still in
-      // flight into this block's shared memory land (bounded), and stop.
+      // flight into or out of this block's shared memory finish (bounded),
+      // and stop.
       if (threadIdx.x == 0) atomicOr(flag, 2u);
-      for (int j = it; j < it + kRowStages; ++j)
+      if (warp == 0) bulk_wait_done();
+      for (int j = it; j < it + kAhead; ++j)
         if (first + j * stride < ntiles) (void)mbar_wait(smem_addr(&bars[j % kRowStages]), (j / kRowStages) & 1);
       return;
     }
-    if (warp == 0 && tile + kRowStages * stride < ntiles) issue(tile + kRowStages * stride, st);
+    if (warp == 0) {
+      store(tile, st);
+      if (kRowStages == 2) {
+        if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, st);
+      } else {
+        if (tile + (kRowStages - 1) * stride < ntiles) issue(tile + (kRowStages - 1) * stride, (it + kRowStages - 1) % kRowStages);
+      }
+    }
   }
+  if (warp == 0) bulk_wait_done();
 }
 
-size_t row_smem_bytes(int nx, size_t elem) { return kRowStages * (kPop * (size_t)nx * elem + sizeof(unsigned long long)); }
+size_t row_smem_bytes(int nx, size_t elem, int stages) {
+  return stages * (kPop * (size_t)nx * elem + sizeof(unsigned long long));
+}
+
+// Stages per row length, from timings of both at 128^3, 256^3 and 512^3
+// (FP16): three stages (the store of a tile drains while the next one is
+// computed) win for rows of 129..256 sites (31.6 against 30.7 GLUPS at
+// 256^3); two win for shorter rows, where more blocks fit per SM (28.6
+// against 28.2 at 128^3), and for 512-site rows, where three stages leave
+// one block per SM (30.1 against 17.5 at 512^3).
+constexpr int row_stages(int nx) { return nx > 128 && nx <= 256 ? 3 : 2; }
 
 // Launch configuration of one instantiation, cached: the shared-memory
 // opt-in and the resident blocks per SM (a function of nx only).
-template <class T, bool ODD, int NX>
+template <class T, bool ODD, int NX, int S>
 cudaError_t row_config(const Grid& g, int* grid, size_t* smem_out) {
-  auto kern = step_row_kernel<T, ODD, NX>;
+  auto kern = step_row_kernel<T, ODD, NX, S>;
   const int threads = g.nx / 2;
-  const size_t smem = row_smem_bytes(g.nx, sizeof(T));
+  const size_t smem = row_smem_bytes(g.nx, sizeof(T), S);
   static size_t attr_smem = 0, occ_smem = 0;
   static int occ = 0;
   cudaError_t e;
@@ -527,27 +598,28 @@ cudaError_t row_maps(const void* pop, const Grid& g, RowMaps* out) {
   return cudaSuccess;
 }
 
-template <class T, bool ODD, int NX>
+template <class T, bool ODD, int NX, int S>
 cudaError_t row_launch(void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch) {
   int grid = 0;
   size_t smem = 0;
-  cudaError_t e = row_config<T, ODD, NX>(g, &grid, &smem);
+  cudaError_t e = row_config<T, ODD, NX, S>(g, &grid, &smem);
   RowMaps maps{};
   if (e == cudaSuccess && g.nx <= kBoxMaxX) e = row_maps(pop, g, &maps);
   if (e != cudaSuccess || !launch) return e;
-  step_row_kernel<T, ODD, NX><<<grid, g.nx / 2, smem, s>>>(make_slots<T>(pop, g), static_cast<const T*>(pop), g, k,
-                                                            flag, maps);
+  step_row_kernel<T, ODD, NX, S><<<grid, g.nx / 2, smem, s>>>(static_cast<T*>(pop), g, k, flag, maps);
   return cudaGetLastError();
 }
 
 template <class T, bool ODD>
 cudaError_t row_nx(void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch) {
   switch (g.nx) {
-    case 64: return row_launch<T, ODD, 64>(pop, g, k, flag, s, launch);
-    case 128: return row_launch<T, ODD, 128>(pop, g, k, flag, s, launch);
-    case 256: return row_launch<T, ODD, 256>(pop, g, k, flag, s, launch);
-    case 512: return row_launch<T, ODD, 512>(pop, g, k, flag, s, launch);
-    default: return row_launch<T, ODD, 0>(pop, g, k, flag, s, launch);
+    case 64: return row_launch<T, ODD, 64, row_stages(64)>(pop, g, k, flag, s, launch);
+    case 128: return row_launch<T, ODD, 128, row_stages(128)>(pop, g, k, flag, s, launch);
+    case 256: return row_launch<T, ODD, 256, row_stages(256)>(pop, g, k, flag, s, launch);
+    case 512: return row_launch<T, ODD, 512, row_stages(512)>(pop, g, k, flag, s, launch);
+    default:
+      return row_stages(g.nx) == 3 ? row_launch<T, ODD, 0, 3>(pop, g, k, flag, s, launch)
+                                   : row_launch<T, ODD, 0, 2>(pop, g, k, flag, s, launch);
   }
 }
 
