@@ -89,9 +89,11 @@ def kernel_name(storage, kernel, n):
 
 
 def recorded_traffic(storage):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_256.md")
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    of that kernel (the row kernel for FP16/BF16, the one-site kernel for
+    FP32), if it was taken on the current kernel source (else None)."""
+    name = "step_row_kernel_256.md" if storage in ("fp16", "bf16") else "step_kernel_256.md"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
@@ -289,6 +291,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--shape", default=None,
+                    help="NX,NY,NZ: a non-cubic lattice of the same recipe (d_i = 0.05 NX), e.g. a smaller "
+                         "case of the 256-site-row kernel for profiling; default n^3")
     ap.add_argument("--impl", default="flame", choices=["flame", "reference"])
     ap.add_argument("--storage", default="fp16,fp32,bf16,fp16/site,bf16/site",
                     help="first entry is the headline; '/site' forces the one-site kernel")
@@ -332,8 +337,12 @@ def main():
         return float(t.item())
 
     n = args.n
-    w = workload(n)
-    u_h, B_h = inputs.turbulence((n, n, n), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
+    nx, ny, nz = (int(v) for v in args.shape.split(",")) if args.shape else (n, n, n)
+    n3 = nx * ny * nz
+    nmin = min(nx, ny, nz)
+    nshell = max(nx, ny, nz) // 2 + 1
+    w = workload(nx)
+    u_h, B_h = inputs.turbulence((nz, ny, nx), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
     u_d = torch.from_numpy(u_h).to(dev)
     B_d = torch.from_numpy(B_h).to(dev)
     storages = [s.strip() for s in args.storage.split(",") if s.strip()]
@@ -345,7 +354,7 @@ def main():
     variants = {}
     for spec in storages:
         st, kern = parse_variant(spec)
-        sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev, kernel=kern)
+        sim = Flame(nx, ny, nz, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev, kernel=kern)
         sim.init(None, u_d, B_d)
         sim.step(args.warmup)
         barrier()
@@ -365,7 +374,7 @@ def main():
             sim.sync()
         except FlameError as ex:
             status = f"nonfinite ({ex.status})"
-        sites = n ** 3
+        sites = n3
         mlups = world * sites * args.steps / (ms_max * 1e-3) / 1e6
         per_launch_s = ms / args.steps * 1e-3
         achieved = BYTES_PER_SITE[st] * sites / per_launch_s / 1e9
@@ -373,7 +382,7 @@ def main():
                           "frac_of_measured_hbm": achieved / peak, "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
                           "algorithmic_bytes_per_site": BYTES_PER_SITE[st],
                           "state_gb": 48 * sites * (4 if st == "fp32" else 2) / 1e9,
-                          "kernel": kernel_name(st, kern, n), "status": status}
+                          "kernel": kernel_name(st, kern, nx), "status": status}
         sim.close()
         del sim
         torch.cuda.empty_cache()
@@ -385,12 +394,12 @@ def main():
     accuracy = {st: {} for st in acc_storages}
     finals = {}
     for st in acc_storages:
-        sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev)
+        sim = Flame(nx, ny, nz, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev)
         sim.init(None, u_d, B_d)
         sim.step(ACC_STEPS)
-        m = sim.moments(out={"u": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
-                             "B": torch.empty((3, n, n, n), dtype=torch.float64, device=dev)})
-        Eu, Eb = sim.spectra(n // 2 + 1)
+        m = sim.moments(out={"u": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
+                             "B": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)})
+        Eu, Eb = sim.spectra(nshell)
         finals[st] = (m["u"], m["B"], Eu, Eb)
         sim.close()
         del sim
@@ -398,7 +407,7 @@ def main():
         ru, rb, rEu, rEb = finals["fp32"]
         for st in acc_storages:
             if st != "fp32":
-                accuracy[st]["vs_fp32_256"] = field_errors(finals[st], finals["fp32"], n, ACC_STEPS)
+                accuracy[st]["vs_fp32_256"] = field_errors(finals[st], finals["fp32"], nmin, ACC_STEPS)
     finals.clear()
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
@@ -409,12 +418,12 @@ def main():
     # fields, flame_init, K steps, D2H of u, B, J and the FP64 scalars.
     pin_u = torch.from_numpy(u_h).pin_memory()
     pin_B = torch.from_numpy(B_h).pin_memory()
-    out_h = torch.empty((9, n, n, n), dtype=torch.float64).pin_memory()
-    sim = Flame(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"], storage=parse_variant(head)[0], device=dev,
+    out_h = torch.empty((9, nz, ny, nx), dtype=torch.float64).pin_memory()
+    sim = Flame(nx, ny, nz, w["tau_nu"], w["tau_eta"], w["d_i"], storage=parse_variant(head)[0], device=dev,
                 kernel=parse_variant(head)[1])
-    outs = {"u": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
-            "B": torch.empty((3, n, n, n), dtype=torch.float64, device=dev),
-            "J": torch.empty((3, n, n, n), dtype=torch.float64, device=dev)}
+    outs = {"u": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
+            "B": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
+            "J": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)}
     barrier()
     t0 = time.perf_counter()
     u_d.copy_(pin_u, non_blocking=True)
@@ -430,9 +439,9 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     barrier()
     sim.close()
-    h2d = 2 * 3 * n ** 3 * 8
-    d2h = 9 * n ** 3 * 8 + 14 * 8
-    e2e = {"value": world * n ** 3 * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    h2d = 2 * 3 * n3 * 8
+    d2h = 9 * n3 * 8 + 14 * 8
+    e2e = {"value": world * n3 * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "job": "pinned host u,B -> device, flame_init, K x flame_step, flame_moments u,B,J -> pinned host, "
                   "flame_reduce scalars", "seconds": e2e_s, "gpu_launches": 1 + args.steps + 1 + 2,
@@ -462,13 +471,15 @@ def main():
         "metric": METRIC, "value": hv["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": hv["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(n, head_st), "n": n, "storage": head_st, "compute": "fp32",
+        "config": {"workload": workload_name(n, head_st) if not args.shape else
+                   f"{nx}x{ny}x{nz} lattice of the same recipe (d_i = {w['d_i']:g}); {head_st.upper()} storage",
+                   "n": n, "shape": [nx, ny, nz], "storage": head_st, "compute": "fp32",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"no flush: the {hv['state_gb']:.2f} GB state streamed each step exceeds the 129 MB L2"},
         "roofline": {"bound": "hbm", "achieved": hv["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": hv["achieved_gbs"] / peak, "traffic": traffic, "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": hv["algorithmic_bytes_per_site"] * n ** 3,
-                     "kernel": kernel_name(head_st, head_kern, n),
+                     "algorithmic_bytes_per_launch": hv["algorithmic_bytes_per_site"] * n3,
+                     "kernel": kernel_name(head_st, head_kern, nx),
                      "frac_of_nominal_8tbs": hv["achieved_gbs"] / NOMINAL_HBM_GBS,
                      "kernel_source_sha256_16": kernel_source_hash()},
         "stated_l2_error": accuracy.get(head, {}).get("vs_oracle_64"),
