@@ -265,6 +265,19 @@ flame_status flame_init_adjoint(flame_ctx *ctx, const double *d_u, const double 
  * FLAME_ERR_CUDA, sticky context errors. */
 flame_status flame_reduce_static(flame_ctx *ctx, int nblocks, double *d_scalars);
 
+/* Test hook for the failure path of the row kernel's waits (the paper has no
+ * counterpart).  The row kernel stages its tiles with copies that complete
+ * on shared-memory barriers, and every wait on a barrier gives up after a
+ * bounded number of polls, sets a flag and ends the launch without writing
+ * the state.  After this call the next flame_step launches one step whose
+ * barriers are armed but never fed (no copy is issued), with a limit of
+ * `tries` polls per wait, synchronises, and returns FLAME_ERR_TIMEOUT
+ * (sticky, like any failure); the state and the step count are left as they
+ * were.  Errors: FLAME_ERR_PARAM (tries == 0, or the context does not run
+ * the row kernel: FP16/BF16 storage, FLAME_SCHEME, kernel = 0, 64 <= nx <=
+ * 512 with nx a multiple of 64), FLAME_ERR_STATE (before flame_init). */
+flame_status flame_debug_stall_next_step(flame_ctx *ctx, unsigned tries);
+
 /* Release the context and its internal workspace (not the caller's state). */
 void flame_destroy(flame_ctx *ctx);
 

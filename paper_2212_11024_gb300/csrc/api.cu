@@ -39,6 +39,7 @@ struct flame_ctx {
   double* d_adj_ws;        // 24 * N3 doubles (initialisation adjoint)
   flame::StepConsts k;
   flame::Grid g;
+  unsigned stall_tries;  // > 0: the next flame_step runs the wait-failure test (flame_debug_stall_next_step)
 };
 
 namespace {
@@ -273,6 +274,15 @@ flame_status flame_step(flame_ctx* c, int n) {
   flame_status st = usable(c);
   if (st != FLAME_OK) return st;
   if (n < 0) return FLAME_ERR_PARAM;
+  if (c->stall_tries && n > 0) {
+    // The wait-failure test: one launch whose waits all run out; it leaves
+    // the state as it was, so step and parity do not advance.
+    cudaError_t e = flame::launch_step_row(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream,
+                                           c->stall_tries);
+    c->stall_tries = 0;
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    return sync_and_check(c);
+  }
   if (!c->initialized) return FLAME_ERR_STATE;
   const int G = c->p.graph_steps;
   while (G > 0 && n >= G) {
@@ -523,6 +533,16 @@ flame_status flame_init_adjoint(flame_ctx* c, const double* d_u, const double* d
   }
   return cuda_fail(c, flame::launch_init_adjoint(c->g, c->k, d_u, d_B, d_adj0, c->d_adj_ws, c->d_adj_partials,
                                                  d_ubar, d_Bbar, d_ddi, c->stream));
+}
+
+flame_status flame_debug_stall_next_step(flame_ctx* c, unsigned tries) {
+  flame_status st = usable(c);
+  if (st != FLAME_OK) return st;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  if (tries == 0 || c->p.kernel != 0 || !flame::step_row_supported(c->g, c->p.storage, c->p.variant, c->state))
+    return FLAME_ERR_PARAM;
+  c->stall_tries = tries;
+  return FLAME_OK;
 }
 
 void flame_destroy(flame_ctx* c) {

@@ -43,8 +43,10 @@ bool step_row_supported(Grid g, int storage, int variant, const void* pop);
 // Settles the launch configuration of the kernel launch_step would use
 // (no launch); needed once before stream capture.
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel);
+// stall_tries > 0: the failure-path test -- the launch arms its barriers
+// without issuing copies and gives up after stall_tries polls per wait.
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                            cudaStream_t s);
+                            cudaStream_t s, unsigned stall_tries = 0);
 
 cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
                         const double* u, const double* B, const double* gu, const double* gB,

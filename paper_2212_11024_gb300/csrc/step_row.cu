@@ -281,8 +281,16 @@ constexpr int kRowMinBlocks = 2;
 // 256 elements wide), longer ones by one bulk copy per row.
 constexpr int kBoxMaxX = 256;
 // mbarrier.try_wait returns after a bounded, hardware-defined time; this
-// many tries (far longer than any copy takes) end the wait with an error.
+// many tries (far longer than any copy takes) end a wait with an error.
 constexpr unsigned kWaitTries = 1u << 22;
+
+// Wait limit and the failure-path test of the waits: with stall set, every
+// stage's barrier is armed for its bytes but no copy is issued, so each wait
+// runs out after `tries` polls (and no copy is ever in flight).
+struct RowWait {
+  unsigned tries;
+  int stall;
+};
 
 // Storage slots come in 16 runs of three (see phys()).  On an odd step run r
 // is staged from the row (y, z) + (dy, dz): the fluid run r = (cy+1) + 3(cz+1)
@@ -311,8 +319,8 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
       : "memory");
   return ok != 0u;
 }
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (unsigned n = 0; n < kWaitTries; ++n)
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned tries) {
+  for (unsigned n = 0; n < tries; ++n)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -396,7 +404,7 @@ struct RowMaps {
 template <class T, bool ODD, int NX, int kRowStages>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
     step_row_kernel(T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
-                    const __grid_constant__ RowMaps maps) {
+                    const __grid_constant__ RowMaps maps, RowWait wt) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nx = NX ? NX : g.nx, ny = g.ny, nz = g.nz;
   const unsigned rowbytes = static_cast<unsigned>(nx) * sizeof(T);
@@ -422,6 +430,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
     T* dst = rows + (size_t)st * kPop * nx;
     if (lane == 0) mbar_expect_tx(bar, kPop * rowbytes);
     __syncwarp();
+    if (wt.stall) return;
     if (boxed) {
       if (!ODD) {
         if (lane == 0) tensor_load(smem_addr(dst), &maps.all, y, z, 0, bar);
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
   int it = 0;
   for (int tile = first; tile < ntiles; tile += stride, ++it) {
     const int st = it % kRowStages;
-    const bool ok = mbar_wait(smem_addr(&bars[st]), (it / kRowStages) & 1);
+    const bool ok = mbar_wait(smem_addr(&bars[st]), (it / kRowStages) & 1, wt.tries);
     if (ok) {
       // Collide in place.  The post-collision value of velocity c belongs in
       // the staged slot of the opposite velocity (on odd steps: the slot of
@@ -504,7 +513,8 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
       if (threadIdx.x == 0) atomicOr(flag, 2u);
       if (warp == 0) bulk_wait_done();
       for (int j = it; j < it + kAhead; ++j)
-        if (first + j * stride < ntiles) (void)mbar_wait(smem_addr(&bars[j % kRowStages]), (j / kRowStages) & 1);
+        if (first + j * stride < ntiles)
+          (void)mbar_wait(smem_addr(&bars[j % kRowStages]), (j / kRowStages) & 1, wt.tries);
       return;
     }
     if (warp == 0) {
@@ -599,33 +609,35 @@ cudaError_t row_maps(const void* pop, const Grid& g, RowMaps* out) {
 }
 
 template <class T, bool ODD, int NX, int S>
-cudaError_t row_launch(void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch) {
+cudaError_t row_launch(void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch,
+                       RowWait wt) {
   int grid = 0;
   size_t smem = 0;
   cudaError_t e = row_config<T, ODD, NX, S>(g, &grid, &smem);
   RowMaps maps{};
   if (e == cudaSuccess && g.nx <= kBoxMaxX) e = row_maps(pop, g, &maps);
   if (e != cudaSuccess || !launch) return e;
-  step_row_kernel<T, ODD, NX, S><<<grid, g.nx / 2, smem, s>>>(static_cast<T*>(pop), g, k, flag, maps);
+  step_row_kernel<T, ODD, NX, S><<<grid, g.nx / 2, smem, s>>>(static_cast<T*>(pop), g, k, flag, maps, wt);
   return cudaGetLastError();
 }
 
 template <class T, bool ODD>
-cudaError_t row_nx(void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch) {
+cudaError_t row_nx(void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch, RowWait wt) {
   switch (g.nx) {
-    case 64: return row_launch<T, ODD, 64, row_stages(64)>(pop, g, k, flag, s, launch);
-    case 128: return row_launch<T, ODD, 128, row_stages(128)>(pop, g, k, flag, s, launch);
-    case 256: return row_launch<T, ODD, 256, row_stages(256)>(pop, g, k, flag, s, launch);
-    case 512: return row_launch<T, ODD, 512, row_stages(512)>(pop, g, k, flag, s, launch);
+    case 64: return row_launch<T, ODD, 64, row_stages(64)>(pop, g, k, flag, s, launch, wt);
+    case 128: return row_launch<T, ODD, 128, row_stages(128)>(pop, g, k, flag, s, launch, wt);
+    case 256: return row_launch<T, ODD, 256, row_stages(256)>(pop, g, k, flag, s, launch, wt);
+    case 512: return row_launch<T, ODD, 512, row_stages(512)>(pop, g, k, flag, s, launch, wt);
     default:
-      return row_stages(g.nx) == 3 ? row_launch<T, ODD, 0, 3>(pop, g, k, flag, s, launch)
-                                   : row_launch<T, ODD, 0, 2>(pop, g, k, flag, s, launch);
+      return row_stages(g.nx) == 3 ? row_launch<T, ODD, 0, 3>(pop, g, k, flag, s, launch, wt)
+                                   : row_launch<T, ODD, 0, 2>(pop, g, k, flag, s, launch, wt);
   }
 }
 
 template <class T>
-cudaError_t row_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch) {
-  return odd ? row_nx<T, true>(pop, g, k, flag, s, launch) : row_nx<T, false>(pop, g, k, flag, s, launch);
+cudaError_t row_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, cudaStream_t s, bool launch,
+                  RowWait wt) {
+  return odd ? row_nx<T, true>(pop, g, k, flag, s, launch, wt) : row_nx<T, false>(pop, g, k, flag, s, launch, wt);
 }
 
 }  // namespace
@@ -636,10 +648,11 @@ bool step_row_supported(Grid g, int storage, int variant, const void* pop) {
 }
 
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                            cudaStream_t s) {
+                            cudaStream_t s, unsigned stall_tries) {
+  const RowWait wt{stall_tries ? stall_tries : kWaitTries, stall_tries ? 1 : 0};
   switch (storage) {
-    case 2: return row_t<__half>(odd, pop, g, k, flag, s, true);
-    case 3: return row_t<__nv_bfloat16>(odd, pop, g, k, flag, s, true);
+    case 2: return row_t<__half>(odd, pop, g, k, flag, s, true, wt);
+    case 3: return row_t<__nv_bfloat16>(odd, pop, g, k, flag, s, true, wt);
   }
   return cudaErrorInvalidValue;
 }
@@ -647,10 +660,11 @@ cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepC
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel) {
   if (kernel != 0 || !step_row_supported(g, storage, variant, pop)) return cudaSuccess;
   const StepConsts k{};
+  const RowWait wt{kWaitTries, 0};
   void* p = const_cast<void*>(pop);
   for (int odd = 0; odd < 2; ++odd) {
-    cudaError_t e = storage == 2 ? row_t<__half>(odd, p, g, k, nullptr, nullptr, false)
-                                 : row_t<__nv_bfloat16>(odd, p, g, k, nullptr, nullptr, false);
+    cudaError_t e = storage == 2 ? row_t<__half>(odd, p, g, k, nullptr, nullptr, false, wt)
+                                 : row_t<__nv_bfloat16>(odd, p, g, k, nullptr, nullptr, false, wt);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

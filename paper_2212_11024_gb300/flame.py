@@ -92,6 +92,7 @@ def _lib():
             "flame_probe": (i, [vp, i, vp, vp]),
             "flame_step_adjoint": (i, [vp, vp, i, vp, vp, vp]),
             "flame_init_adjoint": (i, [vp, vp, vp, vp, vp, vp, vp]),
+            "flame_debug_stall_next_step": (i, [vp, ctypes.c_uint]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +271,11 @@ class Flame:
         Eb = (ctypes.c_double * nshell)()
         _check(self._lib.flame_spectra(self._ctx_or_raise(), int(nshell), Eu, Eb), "flame_spectra")
         return np.array(Eu[:]), np.array(Eb[:])
+
+    def debug_stall_next_step(self, tries=1024):
+        """Arm the wait-failure test for the next step (flame_debug_stall_next_step):
+        that step's waits run out and it raises FlameError(FLAME_ERR_TIMEOUT)."""
+        _check(self._lib.flame_debug_stall_next_step(self._ctx_or_raise(), int(tries)), "flame_debug_stall_next_step")
 
     def get_state(self):
         dst = self.torch.empty_like(self.state)

@@ -76,3 +76,50 @@ def test_row_kernel_graph_replay_is_bit_identical():
     assert a.sync() is None and b.sync() is None
     a.close()
     b.close()
+
+
+def test_row_kernel_wait_limit_reports_timeout():
+    """The row kernel's bounded waits: a step whose barriers are armed but
+    never fed gives FLAME_ERR_TIMEOUT after the poll limit, leaves the state
+    and the step count unchanged, and the GPU stays usable (a fresh context
+    steps and matches a reference run bit for bit)."""
+    import torch
+    from paper_2212_11024_gb300 import Flame, FlameError
+    from paper_2212_11024_gb300.flame import FLAME_ERR_TIMEOUT, FLAME_ERR_PARAM
+    shape = (4, 3, 64)
+    nz, ny, nx = shape
+    u, B = _fields(shape, 47)
+    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0))
+    sim.init(None, u, B)
+    sim.step(3)
+    blob0, step0, par0 = sim.get_state()
+    sim.debug_stall_next_step(256)
+    with pytest.raises(FlameError) as e:
+        sim.step(1)
+    assert e.value.status == FLAME_ERR_TIMEOUT
+    blob1 = torch.empty_like(blob0)
+    import ctypes
+    from paper_2212_11024_gb300.flame import library
+    st, pa = ctypes.c_longlong(), ctypes.c_int()
+    library().flame_get_state(sim._ctx, ctypes.c_void_p(blob1.data_ptr()), ctypes.byref(st), ctypes.byref(pa))
+    torch.cuda.synchronize()
+    assert torch.equal(blob0, blob1) and st.value == step0 and pa.value == par0
+    sim.close()
+    # the site kernel has no such waits: the hook refuses
+    site = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0), kernel="site")
+    site.init(None, u, B)
+    with pytest.raises(FlameError) as e:
+        site.debug_stall_next_step(256)
+    assert e.value.status == FLAME_ERR_PARAM
+    site.close()
+    # a fresh context on the same GPU works: 4 steps equal 3 + 1 restarted
+    a = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0))
+    a.init(None, u, B)
+    a.step(4)
+    b = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0))
+    b.init(None, u, B)
+    b.set_state(blob0, step0, par0)
+    b.step(1)
+    assert torch.equal(a.populations(), b.populations())
+    a.close()
+    b.close()
