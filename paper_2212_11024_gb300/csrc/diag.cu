@@ -1,5 +1,5 @@
 // diag.cu -- kernels that read or write the population state outside the
-// hot path: initialisation from macroscopic fields (FP64), moments and
+// hot path: initialisation from macroscopic fields, moments and
 // decoded populations (FP64), and the deterministic FP64 reduction of the
 // scalar diagnostics.
 #include "aa.cuh"
@@ -8,7 +8,10 @@ namespace flame {
 namespace {
 
 // ---------------------------------------------------------------------------
-// Initialisation (FP64 arithmetic, once per run).
+// Initialisation (once per run).  The arithmetic type R is FP64 for FP32
+// storage and FP32 for 16-bit storage, whose encoding rounds to 2^-11 (FP16)
+// or 2^-8 (BF16) relative, far above FP32's 2^-24; gradients are taken in
+// FP64 from the FP64 fields either way.
 
 __device__ __forceinline__ double cdiff(const double* F, int a, int x, int y, int z, const Grid& g) {
   int xp = x, xm = x, yp = y, ym = y, zp = z, zm = z;
@@ -25,7 +28,7 @@ __device__ __forceinline__ double cdiff(const double* F, int a, int x, int y, in
   return 0.5 * (F[((long long)zp * g.ny + yp) * g.nx + xp] - F[((long long)zm * g.ny + ym) * g.nx + xm]);
 }
 
-template <class T>
+template <class T, class R>
 __global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq, const double* __restrict__ rho_f,
                             const double* __restrict__ u, const double* __restrict__ Bf,
                             const double* __restrict__ gu, const double* __restrict__ gB,
@@ -33,73 +36,89 @@ __global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
-  const long long n3 = g.n3;
-  const long long site = ((long long)z * g.ny + y) * g.nx + x;
-  const double rho = rho_f ? rho_f[site] : 1.0;
-  const double U[3] = {u[site], u[n3 + site], u[2 * n3 + site]};
-  const double B[3] = {Bf[site], Bf[n3 + site], Bf[2 * n3 + site]};
-  double du[9], dB[9];
+  const bool in = x < g.nx && y < g.ny;
+  float sp = 0.f;
+  if (in) {
+    const long long n3 = g.n3;
+    const long long site = ((long long)z * g.ny + y) * g.nx + x;
+    const R rho = rho_f ? (R)rho_f[site] : (R)1;
+    const R U[3] = {(R)u[site], (R)u[n3 + site], (R)u[2 * n3 + site]};
+    const R B[3] = {(R)Bf[site], (R)Bf[n3 + site], (R)Bf[2 * n3 + site]};
+    R du[9], dB[9];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      du[3 * a + b] = gu ? gu[(3 * a + b) * n3 + site] : cdiff(u + b * n3, a, x, y, z, g);
-      dB[3 * a + b] = gB ? gB[(3 * a + b) * n3 + site] : cdiff(Bf + b * n3, a, x, y, z, g);
-    }
-  const double J0[3] = {dB[5] - dB[7], dB[6] - dB[2], dB[1] - dB[3]};  // curl B
-  const double omega = (double)k.omega, omegaB = (double)k.omegaB, aH = (double)k.alphaH;
-  const double Br[3] = {(double)k.Bref[0], (double)k.Bref[1], (double)k.Bref[2]};
-  const double b[3] = {B[0] - Br[0], B[1] - Br[1], B[2] - Br[2]};
-  double N[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) N[a][c] = Br[a] * b[c] + b[a] * Br[c] + b[a] * b[c];
-  const double miso = Br[0] * b[0] + Br[1] * b[1] + Br[2] * b[2] + 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-  const double trN3 = (N[0][0] + N[1][1] + N[2][2]) / 3.0;
-  double Pn[3][3];  // first-order non-equilibrium stress -(rho cs^2/omega)(du + du^T)
-  for (int a = 0; a < 3; ++a)
-    for (int c = 0; c < 3; ++c) Pn[a][c] = noneq ? -(rho / (3.0 * omega)) * (du[3 * a + c] + du[3 * c + a]) : 0.0;
-  const double trPn3 = (Pn[0][0] + Pn[1][1] + Pn[2][2]) / 3.0;
-  const double drho = rho - (double)k.rho0;
-#pragma unroll 1
-  for (int i = 0; i < kQ; ++i) {
-    const int c[3] = {cx27(i), cy27(i), cz27(i)};
-    double E = 0.0;  // prod(psi/w1) - 1, accumulated stably
-    for (int a = 0; a < 3; ++a) {
-      const double uu = U[a] * U[a];
-      const double ea = c[a] == 0 ? -1.5 * uu : 3.0 * uu + 3.0 * c[a] * U[a];
-      E = E + ea + E * ea;
-    }
-    double cNc = 0.0, cPc = 0.0;
     for (int a = 0; a < 3; ++a)
-      for (int d = 0; d < 3; ++d) {
-        cNc += c[a] * c[d] * N[a][d];
-        cPc += c[a] * c[d] * Pn[a][d];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        du[3 * a + b] = (R)(gu ? gu[(3 * a + b) * n3 + site] : cdiff(u + b * n3, a, x, y, z, g));
+        dB[3 * a + b] = (R)(gB ? gB[(3 * a + b) * n3 + site] : cdiff(Bf + b * n3, a, x, y, z, g));
       }
-    const double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-    const double L = 4.5 * (miso * (c2 - 1.0) - cNc + trN3);
-    const double ne = 4.5 * (cPc - trPn3);
-    pop[(long long)phys(i) * n3 + site] = Codec<T>::enc((float)(drho + rho * E + L + ne));
-  }
-  const double V[3] = {U[0] - aH * J0[0], U[1] - aH * J0[1], U[2] - aH * J0[2]};
-  for (int bb = 0; bb < 3; ++bb)
-    for (int i = 0; i < kM; ++i) {
-      const int xi[3] = {mx7(i), my7(i), mz7(i)};
-      double l0 = 0.0, ne = 0.0;
+    const R J0[3] = {dB[5] - dB[7], dB[6] - dB[2], dB[1] - dB[3]};  // curl B
+    const R omega = (R)k.omega, omegaB = (R)k.omegaB, aH = (R)k.alphaH;
+    const R Br[3] = {(R)k.Bref[0], (R)k.Bref[1], (R)k.Bref[2]};
+    const R b[3] = {B[0] - Br[0], B[1] - Br[1], B[2] - Br[2]};
+    R N[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) N[a][c] = Br[a] * b[c] + b[a] * Br[c] + b[a] * b[c];
+    const R miso = Br[0] * b[0] + Br[1] * b[1] + Br[2] * b[2] + (R)0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const R trN3 = (N[0][0] + N[1][1] + N[2][2]) / (R)3;
+    R Pn[3][3];  // first-order non-equilibrium stress -(rho cs^2/omega)(du + du^T)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Pn[a][c] = noneq ? -(rho / ((R)3 * omega)) * (du[3 * a + c] + du[3 * c + a]) : (R)0;
+    const R trPn3 = (Pn[0][0] + Pn[1][1] + Pn[2][2]) / (R)3;
+    const R drho = rho - (R)k.rho0;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int c[3] = {cx27(i), cy27(i), cz27(i)};
+      R E = 0;  // prod(psi/w1) - 1, accumulated stably
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
-        l0 += xi[a] * (V[a] * B[bb] - B[a] * V[bb]);
-        ne += xi[a] * dB[3 * a + bb];
+        const R uu = U[a] * U[a];
+        const R ea = c[a] == 0 ? (R)-1.5 * uu : (R)3 * uu + (R)(3 * c[a]) * U[a];
+        E = E + ea + E * ea;
       }
-      const double v = b[bb] + 4.0 * l0 - (noneq ? ne / omegaB : 0.0);
-      pop[(long long)phys(mslot(bb, i)) * n3 + site] = Codec<T>::enc((float)v);
+      R cNc = 0, cPc = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (c[a] * c[d] == 0) continue;
+          cNc += (R)(c[a] * c[d]) * N[a][d];
+          cPc += (R)(c[a] * c[d]) * Pn[a][d];
+        }
+      const R c2 = (R)(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+      const R L = (R)4.5 * (miso * (c2 - (R)1) - cNc + trN3);
+      const R ne = (R)4.5 * (cPc - trPn3);
+      pop[(long long)phys(i) * n3 + site] = Codec<T>::enc((float)(drho + rho * E + L + ne));
     }
-  const double va = sqrt((B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho);
-  const double um = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-  const float sp = (float)fmax(va, um);
-  if (isfinite(sp)) atomicMax(speed_bits, __float_as_uint(sp));
-  else atomicMax(speed_bits, 0x7f800000u);
+    const R V[3] = {U[0] - aH * J0[0], U[1] - aH * J0[1], U[2] - aH * J0[2]};
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+      for (int i = 0; i < kM; ++i) {
+        const int xi[3] = {mx7(i), my7(i), mz7(i)};
+        R l0 = 0, ne = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (xi[a] == 0) continue;
+          l0 += (R)xi[a] * (V[a] * B[bb] - B[a] * V[bb]);
+          ne += (R)xi[a] * dB[3 * a + bb];
+        }
+        const R v = b[bb] + (R)4 * l0 - (noneq ? ne / omegaB : (R)0);
+        pop[(long long)phys(mslot(bb, i)) * n3 + site] = Codec<T>::enc((float)v);
+      }
+    const R va = sqrt((B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho);
+    const R um = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    sp = (float)fmax(va, um);
+    if (!isfinite(sp)) sp = __uint_as_float(0x7f800000u);
+  }
+  // max speed: one atomic per warp (non-negative floats order like their bits)
+  const unsigned m = __reduce_max_sync(0xffffffffu, in ? __float_as_uint(sp) : 0u);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(speed_bits, m);
 }
-
 
 // ---------------------------------------------------------------------------
 // Moments and decoded populations (FP64 arithmetic from the stored values).
@@ -347,9 +366,9 @@ cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int
                         unsigned* speed_bits, cudaStream_t s) {
   const dim3 b = site_block(g), gr = site_grid(g, b);
   switch (storage) {
-    case 1: init_kernel<float><<<gr, b, 0, s>>>(static_cast<float*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    case 2: init_kernel<__half><<<gr, b, 0, s>>>(static_cast<__half*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    case 3: init_kernel<__nv_bfloat16><<<gr, b, 0, s>>>(static_cast<__nv_bfloat16*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
+    case 1: init_kernel<float, double><<<gr, b, 0, s>>>(static_cast<float*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
+    case 2: init_kernel<__half, float><<<gr, b, 0, s>>>(static_cast<__half*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
+    case 3: init_kernel<__nv_bfloat16, float><<<gr, b, 0, s>>>(static_cast<__nv_bfloat16*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
