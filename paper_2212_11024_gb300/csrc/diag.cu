@@ -121,57 +121,79 @@ __global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq
 }
 
 // ---------------------------------------------------------------------------
-// Moments and decoded populations (FP64 arithmetic from the stored values).
+// Moments and decoded populations.  Per-site arithmetic in R: FP64 for FP32
+// storage, FP32 for 16-bit storage (whose stored values carry 11 or 8
+// significant bits).  Density and field are formed as deviations from the
+// reference (rho0, B_ref) and added to it in FP64, so sums over sites keep
+// the FP64 reference exact.
 
-template <class T, bool ODD>
+template <class T, bool ODD, class R>
 __device__ __forceinline__ void load_site(const T* __restrict__ pop, int site, const Nbr& nb, long long n3,
-                                          double sf[kQ], double sg[3][kM]) {
+                                          R sf[kQ], R sg[3][kM]) {
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) sf[i] = (double)Codec<T>::dec(pop[src27<ODD>(i, site, nb, n3)]);
+  for (int i = 0; i < kQ; ++i) sf[i] = (R)Codec<T>::dec(pop[src27<ODD>(i, site, nb, n3)]);
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int i = 0; i < kM; ++i) sg[b][i] = (double)Codec<T>::dec(pop[src7<ODD>(b, i, site, nb, n3)]);
+    for (int i = 0; i < kM; ++i) sg[b][i] = (R)Codec<T>::dec(pop[src7<ODD>(b, i, site, nb, n3)]);
 }
 
+template <class R>
 struct SiteMoments {
-  double rho, U[3], B[3], J[3], trlam;
+  R drho, U[3], dB[3], J[3], trlam;  // drho = rho - rho0, dB = B - B_ref
+  __device__ __forceinline__ double rho(const StepConsts& k) const { return (double)k.rho0 + (double)drho; }
+  __device__ __forceinline__ double B(const StepConsts& k, int a) const { return (double)k.Bref[a] + (double)dB[a]; }
 };
 
-__device__ __forceinline__ SiteMoments site_moments(const double sf[kQ], const double sg[3][kM], const StepConsts& k) {
-  SiteMoments m;
-  double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
+template <class R>
+__device__ __forceinline__ SiteMoments<R> site_moments(const R sf[kQ], const R sg[3][kM], const StepConsts& k) {
+  SiteMoments<R> m;
+  R drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const double t = w27d(i) * sf[i];
+    const R t = (R)w27d(i) * sf[i];
     drho += t;
-    j[0] += cx27(i) * t;
-    j[1] += cy27(i) * t;
-    j[2] += cz27(i) * t;
+    if (cx27(i)) j[0] += (R)cx27(i) * t;
+    if (cy27(i)) j[1] += (R)cy27(i) * t;
+    if (cz27(i)) j[2] += (R)cz27(i) * t;
   }
-  m.rho = (double)k.rho0 + drho;
-  for (int a = 0; a < 3; ++a) m.U[a] = j[a] / m.rho;
-  double lam[3][3];
+  m.drho = drho;
+  const R rho = (R)k.rho0 + drho;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) m.U[a] = j[a] / rho;
+  R lam[3][3];
+#pragma unroll
   for (int b = 0; b < 3; ++b) {
-    m.B[b] = (double)k.Bref[b] + 0.25 * sg[b][0] + 0.125 * (sg[b][1] + sg[b][2] + sg[b][3] + sg[b][4] + sg[b][5] + sg[b][6]);
-    lam[0][b] = 0.125 * (sg[b][1] - sg[b][2]);
-    lam[1][b] = 0.125 * (sg[b][3] - sg[b][4]);
-    lam[2][b] = 0.125 * (sg[b][5] - sg[b][6]);
+    m.dB[b] = (R)0.25 * sg[b][0] + (R)0.125 * (sg[b][1] + sg[b][2] + sg[b][3] + sg[b][4] + sg[b][5] + sg[b][6]);
+    lam[0][b] = (R)0.125 * (sg[b][1] - sg[b][2]);
+    lam[1][b] = (R)0.125 * (sg[b][3] - sg[b][4]);
+    lam[2][b] = (R)0.125 * (sg[b][5] - sg[b][6]);
   }
   m.trlam = lam[0][0] + lam[1][1] + lam[2][2];
-  const double gq = 4.0 * (double)k.omegaB;
-  const double* U = m.U;
-  const double* B = m.B;
-  const double A[3] = {lam[1][2] - lam[2][1], lam[2][0] - lam[0][2], lam[0][1] - lam[1][0]};
-  const double uxb[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2], U[0] * B[1] - U[1] * B[0]};
-  const double yv[3] = {-gq * (A[0] - 2.0 * uxb[0]), -gq * (A[1] - 2.0 * uxb[1]), -gq * (A[2] - 2.0 * uxb[2])};
-  const double s = 2.0 * (double)k.alphaH * gq;
-  const double yxb[3] = {yv[1] * B[2] - yv[2] * B[1], yv[2] * B[0] - yv[0] * B[2], yv[0] * B[1] - yv[1] * B[0]};
-  const double yb = yv[0] * B[0] + yv[1] * B[1] + yv[2] * B[2];
-  const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-  for (int a = 0; a < 3; ++a) m.J[a] = (yv[a] - s * yxb[a] + s * s * yb * B[a]) / (1.0 + s * s * b2);
+  const R gq = (R)4 * (R)k.omegaB;
+  const R* U = m.U;
+  const R B[3] = {(R)k.Bref[0] + m.dB[0], (R)k.Bref[1] + m.dB[1], (R)k.Bref[2] + m.dB[2]};
+  const R A[3] = {lam[1][2] - lam[2][1], lam[2][0] - lam[0][2], lam[0][1] - lam[1][0]};
+  const R uxb[3] = {U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2], U[0] * B[1] - U[1] * B[0]};
+  const R yv[3] = {-gq * (A[0] - (R)2 * uxb[0]), -gq * (A[1] - (R)2 * uxb[1]), -gq * (A[2] - (R)2 * uxb[2])};
+  const R s = (R)2 * (R)k.alphaH * gq;
+  const R yxb[3] = {yv[1] * B[2] - yv[2] * B[1], yv[2] * B[0] - yv[0] * B[2], yv[0] * B[1] - yv[1] * B[0]};
+  const R yb = yv[0] * B[0] + yv[1] * B[1] + yv[2] * B[2];
+  const R b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) m.J[a] = (yv[a] - s * yxb[a] + s * s * yb * B[a]) / ((R)1 + s * s * b2);
   return m;
 }
+
+// per-site arithmetic type of a storage type
+template <class T>
+struct SiteReal {
+  using type = float;
+};
+template <>
+struct SiteReal<float> {
+  using type = double;
+};
 
 template <class T, bool ODD>
 __global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, double* __restrict__ rho,
@@ -182,14 +204,15 @@ __global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, 
   if (x >= g.nx || y >= g.ny) return;
   const int site = (z * g.ny + y) * g.nx + x;
   const Nbr nb = make_nbr(x, y, z, g);
-  double sf[kQ], sg[3][kM];
+  using R = typename SiteReal<T>::type;
+  R sf[kQ], sg[3][kM];
   load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
-  const SiteMoments m = site_moments(sf, sg, k);
-  if (rho) rho[site] = m.rho;
+  const SiteMoments<R> m = site_moments(sf, sg, k);
+  if (rho) rho[site] = m.rho(k);
   for (int a = 0; a < 3; ++a) {
-    if (u) u[a * g.n3 + site] = m.U[a];
-    if (B) B[a * g.n3 + site] = m.B[a];
-    if (J) J[a * g.n3 + site] = m.J[a];
+    if (u) u[a * g.n3 + site] = (double)m.U[a];
+    if (B) B[a * g.n3 + site] = m.B(k, a);
+    if (J) J[a * g.n3 + site] = (double)m.J[a];
   }
 }
 
@@ -202,7 +225,7 @@ __global__ void populations_kernel(const T* __restrict__ pop, Grid g, StepConsts
   const int site = (z * g.ny + y) * g.nx + x;
   const Nbr nb = make_nbr(x, y, z, g);
   double sf[kQ], sg[3][kM];
-  load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
+  load_site<T, ODD, double>(pop, site, nb, g.n3, sf, sg);
   const double Br[3] = {(double)k.Bref[0], (double)k.Bref[1], (double)k.Bref[2]};
   const double br2 = Br[0] * Br[0] + Br[1] * Br[1] + Br[2] * Br[2];
 #pragma unroll 1
@@ -231,15 +254,16 @@ __global__ void probe_kernel(const T* __restrict__ pop, Grid g, StepConsts k, in
   const int site = (int)sl;
   const int x = site % g.nx, y = (site / g.nx) % g.ny, z = site / (g.nx * g.ny);
   const Nbr nb = make_nbr(x, y, z, g);
-  double sf[kQ], sg[3][kM];
+  using R = typename SiteReal<T>::type;
+  R sf[kQ], sg[3][kM];
   load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
-  const SiteMoments m = site_moments(sf, sg, k);
+  const SiteMoments<R> m = site_moments(sf, sg, k);
   double* o = out + (long long)j * 10;
-  o[0] = m.rho;
+  o[0] = m.rho(k);
   for (int a = 0; a < 3; ++a) {
-    o[1 + a] = m.U[a];
-    o[4 + a] = m.B[a];
-    o[7 + a] = m.J[a];
+    o[1 + a] = (double)m.U[a];
+    o[4 + a] = m.B(k, a);
+    o[7 + a] = (double)m.J[a];
   }
 }
 
@@ -270,29 +294,31 @@ __global__ void reduce_kernel(const T* __restrict__ pop, Grid g, StepConsts k, d
     const int site = (int)s;
     const int x = site % g.nx, y = (site / g.nx) % g.ny, z = site / (g.nx * g.ny);
     const Nbr nb = make_nbr(x, y, z, g);
-    double sf[kQ], sg[3][kM];
+    using R = typename SiteReal<T>::type;
+    R sf[kQ], sg[3][kM];
     load_site<T, ODD>(pop, site, nb, n3, sf, sg);
-    const SiteMoments m = site_moments(sf, sg, k);
-    const double b[3] = {m.B[0] - k.Bref[0], m.B[1] - k.Bref[1], m.B[2] - k.Bref[2]};
-    const double uu = m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2];
-    const double dv = 4.0 * (double)k.omegaB * m.trlam;
-    const bool ok = isfinite(m.rho + uu + b[0] + b[1] + b[2] + m.J[0] + m.J[1] + m.J[2]);
+    const SiteMoments<R> m = site_moments(sf, sg, k);
+    const R* b = m.dB;
+    const R uu = m.U[0] * m.U[0] + m.U[1] * m.U[1] + m.U[2] * m.U[2];
+    const R dv = (R)4 * (R)k.omegaB * m.trlam;
+    const bool ok = isfinite(m.drho + uu + b[0] + b[1] + b[2] + m.J[0] + m.J[1] + m.J[2]);
     if (!ok) {
       acc[16] += 1.0;
       continue;
     }
-    acc[0] += m.rho;
+    const double rho = m.rho(k);
+    acc[0] += rho;
     for (int a = 0; a < 3; ++a) {
-      acc[1 + a] += m.rho * m.U[a];
-      acc[4 + a] += m.B[a];
-      acc[10 + a] += m.U[a];
+      acc[1 + a] += rho * (double)m.U[a];
+      acc[4 + a] += m.B(k, a);
+      acc[10 + a] += (double)m.U[a];
     }
-    acc[7] += uu;
-    acc[8] += b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-    acc[9] += m.U[0] * b[0] + m.U[1] * b[1] + m.U[2] * b[2];
-    acc[13] += m.J[0] * m.J[0] + m.J[1] * m.J[1] + m.J[2] * m.J[2];
-    acc[14] = fmax(acc[14], sqrt(uu));
-    acc[15] += dv * dv;
+    acc[7] += (double)uu;
+    acc[8] += (double)(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    acc[9] += (double)(m.U[0] * b[0] + m.U[1] * b[1] + m.U[2] * b[2]);
+    acc[13] += (double)(m.J[0] * m.J[0] + m.J[1] * m.J[1] + m.J[2] * m.J[2]);
+    acc[14] = fmax(acc[14], sqrt((double)uu));
+    acc[15] += (double)(dv * dv);
   }
   // warp, then block
   __shared__ double sh[32][kRedVals];
