@@ -401,8 +401,84 @@ struct RowMaps {
   CUtensorMap all, run;
 };
 
+// Warp 0 moves the 48 rows of tile (y, z) between HBM and stage st: the rows
+// (y, z) of all storage slots on even steps, run r of three storage slots
+// from the row (y, z) + (run_dy(r), run_dz(r)) on odd steps.  The store
+// writes each row back to where it was loaded from.
+template <class T, bool ODD>
+struct RowIO {
+  T* state;
+  T* rows;  // [stage][48 storage slots][nx]
+  unsigned long long* bars;
+  long long n3;
+  int nx, ny, nz;
+  unsigned rowbytes;
+  int lane;
+  bool boxed, stall;
+  const RowMaps* maps;
+
+  __device__ __forceinline__ void issue(int tile, int st) const {
+    const int y = tile % ny, z = tile / ny;
+    const unsigned bar = smem_addr(&bars[st]);
+    T* dst = rows + (size_t)st * kPop * nx;
+    if (lane == 0) mbar_expect_tx(bar, kPop * rowbytes);
+    __syncwarp();
+    if (stall) return;
+    if (boxed) {
+      if (!ODD) {
+        if (lane == 0) tensor_load(smem_addr(dst), &maps->all, y, z, 0, bar);
+      } else if (lane < kRuns) {
+        tensor_load(smem_addr(dst + 3 * lane * nx), &maps->run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz),
+                    3 * lane, bar);
+      }
+    } else {
+      for (int s = lane; s < kPop; s += 32) {
+        const int r = s / 3;
+        const int ys = ODD ? wrap(y + run_dy(r), ny) : y, zs = ODD ? wrap(z + run_dz(r), nz) : z;
+        bulk_load(smem_addr(dst + s * nx), state + (size_t)s * n3 + ((long long)zs * ny + ys) * nx, rowbytes, bar);
+      }
+    }
+  }
+
+  // Returns once the stage has been read out as far as its refill needs.
+  template <int STAGES>
+  __device__ __forceinline__ void store(int tile, int st) const {
+    const int y = tile % ny, z = tile / ny;
+    const T* src = rows + (size_t)st * kPop * nx;
+    if (boxed) {
+      if (!ODD) {
+        if (lane == 0) tensor_store(&maps->all, y, z, 0, smem_addr(src));
+      } else if (lane < kRuns) {
+        tensor_store(&maps->run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz), 3 * lane,
+                     smem_addr(src + 3 * lane * nx));
+      }
+    } else {
+      for (int s = lane; s < kPop; s += 32) {
+        const int r = s / 3;
+        const int ys = ODD ? wrap(y + run_dy(r), ny) : y, zs = ODD ? wrap(z + run_dz(r), nz) : z;
+        bulk_store(state + (size_t)s * n3 + ((long long)zs * ny + ys) * nx, smem_addr(src + s * nx), rowbytes);
+      }
+    }
+    bulk_commit();
+    // Two stages: this stage is refilled next, so its rows must have been
+    // read out.  Three: the stage refilled next held the previous tile,
+    // whose store is the older of the two groups in flight.
+    if (STAGES == 2) bulk_wait_read();
+    else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    __syncwarp();
+  }
+};
+
+// Launch bounds per instantiation: a 256-site row (128 threads) with three
+// stages fits three blocks per SM by shared memory, so it may use up to 168
+// registers per thread at no cost in occupancy; the others stay at 128.
+constexpr int row_bound_threads(int nx) { return nx ? nx / 2 : kRowMaxThreads; }
+constexpr int row_bound_blocks(int nx, int stages) {
+  return nx == 256 && stages == 3 ? 3 : kRowMinBlocks * kRowMaxThreads / row_bound_threads(nx);
+}
+
 template <class T, bool ODD, int NX, int kRowStages>
-__global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
+__global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kRowStages))
     step_row_kernel(T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
                     const __grid_constant__ RowMaps maps, RowWait wt) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -420,57 +496,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
   }
   __syncthreads();
 
-  // Warp 0 moves the 48 rows of tile (y, z) between HBM and stage st: the
-  // rows (y, z) of all storage slots on even steps, run r of three storage
-  // slots from the row (y, z) + (run_dy(r), run_dz(r)) on odd steps.  The
-  // store writes each row back to where it was loaded from.
-  auto issue = [&](int tile, int st) {
-    const int y = tile % ny, z = tile / ny;
-    const unsigned bar = smem_addr(&bars[st]);
-    T* dst = rows + (size_t)st * kPop * nx;
-    if (lane == 0) mbar_expect_tx(bar, kPop * rowbytes);
-    __syncwarp();
-    if (wt.stall) return;
-    if (boxed) {
-      if (!ODD) {
-        if (lane == 0) tensor_load(smem_addr(dst), &maps.all, y, z, 0, bar);
-      } else if (lane < kRuns) {
-        tensor_load(smem_addr(dst + 3 * lane * nx), &maps.run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz),
-                    3 * lane, bar);
-      }
-    } else {
-      for (int s = lane; s < kPop; s += 32) {
-        const int r = s / 3;
-        const int ys = ODD ? wrap(y + run_dy(r), ny) : y, zs = ODD ? wrap(z + run_dz(r), nz) : z;
-        bulk_load(smem_addr(dst + s * nx), state + (size_t)s * g.n3 + ((long long)zs * ny + ys) * nx, rowbytes, bar);
-      }
-    }
-  };
-  auto store = [&](int tile, int st) {  // returns once the stage has been read
-    const int y = tile % ny, z = tile / ny;
-    const T* src = rows + (size_t)st * kPop * nx;
-    if (boxed) {
-      if (!ODD) {
-        if (lane == 0) tensor_store(&maps.all, y, z, 0, smem_addr(src));
-      } else if (lane < kRuns) {
-        tensor_store(&maps.run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz), 3 * lane,
-                     smem_addr(src + 3 * lane * nx));
-      }
-    } else {
-      for (int s = lane; s < kPop; s += 32) {
-        const int r = s / 3;
-        const int ys = ODD ? wrap(y + run_dy(r), ny) : y, zs = ODD ? wrap(z + run_dz(r), nz) : z;
-        bulk_store(state + (size_t)s * g.n3 + ((long long)zs * ny + ys) * nx, smem_addr(src + s * nx), rowbytes);
-      }
-    }
-    bulk_commit();
-    // Two stages: this stage is refilled next, so its rows must have been
-    // read out.  Three: the stage refilled next held the previous tile,
-    // whose store is the older of the two groups in flight.
-    if (kRowStages == 2) bulk_wait_read();
-    else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-    __syncwarp();
-  };
+  const RowIO<T, ODD> io{state, rows, bars, g.n3, nx, ny, nz, rowbytes, lane, boxed, wt.stall != 0, &maps};
 
   const int first = blockIdx.x, stride = gridDim.x;
   // Tiles staged before the loop: both stages with two; with three, two of
@@ -478,7 +504,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
   constexpr int kAhead = kRowStages == 2 ? 2 : kRowStages - 1;
   if (warp == 0)
     for (int s = 0; s < kAhead; ++s)
-      if (first + s * stride < ntiles) issue(first + s * stride, s);
+      if (first + s * stride < ntiles) io.issue(first + s * stride, s);
 
   int it = 0;
   for (int tile = first; tile < ntiles; tile += stride, ++it) {
@@ -518,11 +544,11 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowMinBlocks)
       return;
     }
     if (warp == 0) {
-      store(tile, st);
+      io.template store<kRowStages>(tile, st);
       if (kRowStages == 2) {
-        if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, st);
+        if (tile + 2 * stride < ntiles) io.issue(tile + 2 * stride, st);
       } else {
-        if (tile + (kRowStages - 1) * stride < ntiles) issue(tile + (kRowStages - 1) * stride, (it + kRowStages - 1) % kRowStages);
+        if (tile + (kRowStages - 1) * stride < ntiles) io.issue(tile + (kRowStages - 1) * stride, (it + kRowStages - 1) % kRowStages);
       }
     }
   }
