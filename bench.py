@@ -136,6 +136,11 @@ class ClockSampler:
     def window(self, t0, t1):
         self.windows.append((t0, t1))
 
+    def median_in(self, t0, t1):
+        """Median SM clock (MHz) of the samples taken between t0 and t1."""
+        sm = [float(s[1]) for t, s in self.samples if t0 <= t <= t1 and s[1].replace(".", "", 1).isdigit()]
+        return statistics.median(sm) if sm else None
+
     def stop(self):
         if self.proc is None:
             return None
@@ -425,18 +430,32 @@ def main():
             "B": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
             "J": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)}
     barrier()
+    t_wall0 = time.time()
     t0 = time.perf_counter()
+    marks = [t0]
+
+    def mark():  # phase boundaries (a stream synchronisation each; the job's own calls synchronise anyway)
+        torch.cuda.synchronize(dev)
+        marks.append(time.perf_counter())
+
     u_d.copy_(pin_u, non_blocking=True)
     B_d.copy_(pin_B, non_blocking=True)
+    mark()
     sim.init(None, u_d, B_d)
+    mark()
     sim.step(args.steps)
+    mark()
     sim.moments(out=outs)
     out_h[0:3].copy_(outs["u"], non_blocking=True)
     out_h[3:6].copy_(outs["B"], non_blocking=True)
     out_h[6:9].copy_(outs["J"], non_blocking=True)
+    mark()
     scal = sim.reduce()
     torch.cuda.synchronize(dev)
+    marks.append(time.perf_counter())
     e2e_s = max_over_ranks(time.perf_counter() - t0)
+    clocks.window(t_wall0, time.time())
+    e2e_sm = clocks.median_in(t_wall0, time.time())
     barrier()
     sim.close()
     h2d = 2 * 3 * n3 * 8
@@ -445,7 +464,10 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "job": "pinned host u,B -> device, flame_init, K x flame_step, flame_moments u,B,J -> pinned host, "
                   "flame_reduce scalars", "seconds": e2e_s, "gpu_launches": 1 + args.steps + 1 + 2,
-           "final_E_u": scal["E_u"], "final_E_B": scal["E_B"]}
+           "final_E_u": scal["E_u"], "final_E_B": scal["E_B"],
+           "phases_ms": {k: (marks[i + 1] - marks[i]) * 1e3 for i, k in
+                         enumerate(("h2d", "init", "steps", "moments_d2h", "reduce"))},
+           "sm_mhz": e2e_sm}
     clk = clocks.stop()
 
     if dist is not None:
