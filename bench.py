@@ -68,10 +68,16 @@ def hbm_peak():
 
 
 def kernel_source_hash():
+    """SHA-256 (first 16 hex digits) of the step kernels' sources with comments
+    and whitespace removed, so that only a change of the code itself
+    invalidates a recorded ncu traffic figure."""
     h = hashlib.sha256()
     for f in ("step.cu", "step_row.cu", "lattice.cuh", "aa.cuh"):
-        with open(os.path.join(ROOT, "paper_2212_11024_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2212_11024_gb300", "csrc", f)) as fh:
+            txt = fh.read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        h.update(re.sub(r"\s+", "", txt).encode())
     return h.hexdigest()[:16]
 
 

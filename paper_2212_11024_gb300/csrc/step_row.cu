@@ -272,9 +272,8 @@ __device__ __forceinline__ void collide_pair(const LdF& ldf, const LdG& ldg, con
 }
 
 // ------------------------------------------- rows staged by TMA, persistent
-// At most 256 threads (nx <= 512) and 128 registers per thread (two
-// 256-thread blocks per SM; 210 registers, the unconstrained allocation,
-// leave fewer warps and ran slower at 256^3).  Stages: row_stages().
+// At most 256 threads per block (nx <= 512); launch bounds per instantiation
+// (row_bound_threads / row_bound_blocks below); stages: row_stages().
 constexpr int kRowMaxThreads = 256;
 constexpr int kRowMinBlocks = 2;
 // Rows up to this length are staged by tensor-map copies (a box is at most
@@ -362,9 +361,9 @@ __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >=
 
 // The site pair (2t, 2t + 1) of a staged tile: ld(s, d) reads staged
 // storage slot s at the pair moved by d sites (d = -c_x reads velocity c on
-// an odd step; d = 0 on even steps), st(s, d, v) writes it there.  NX > 0 fixes the row length at compile
-// time (shared-memory offsets become immediates); NX = 0 reads it from the
-// grid.
+// an odd step; d = 0 on even steps), st(s, d, v) writes it there.  NX > 0
+// fixes the row length at compile time (shared-memory offsets become
+// immediates); NX = 0 reads it from the grid.
 template <class T, bool ODD, int NX>
 struct PairAccess {
   const T* R;
