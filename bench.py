@@ -295,6 +295,25 @@ def oracle_restriction_errors(storages, dev):
     return out
 
 
+# --------------------------------------------------------------------------- replicas (N > 1)
+def reduce_max(x, dist=None, device=None):
+    """The largest x over the ranks of the default process group (x itself
+    without one): every rank gets the slowest rank's time."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(world, sites, steps, seconds):
+    """Whole-job throughput of `world` independent replicas, each updating
+    `sites` sites `steps` times, over the slowest replica's time."""
+    return world * sites * steps / seconds / 1e6
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -341,11 +360,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, dev)
 
     n = args.n
     nx, ny, nz = (int(v) for v in args.shape.split(",")) if args.shape else (n, n, n)
@@ -386,7 +401,7 @@ def main():
         except FlameError as ex:
             status = f"nonfinite ({ex.status})"
         sites = n3
-        mlups = world * sites * args.steps / (ms_max * 1e-3) / 1e6
+        mlups = replica_mlups(world, sites, args.steps, ms_max * 1e-3)
         per_launch_s = ms / args.steps * 1e-3
         achieved = BYTES_PER_SITE[st] * sites / per_launch_s / 1e9
         variants[spec] = {"mlups": mlups, "ms_per_step": ms_max / args.steps, "achieved_gbs": achieved,
@@ -466,7 +481,7 @@ def main():
     sim.close()
     h2d = 2 * 3 * n3 * 8
     d2h = 9 * n3 * 8 + 14 * 8
-    e2e = {"value": world * n3 * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": replica_mlups(world, n3, args.steps, e2e_s), "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "job": "pinned host u,B -> device, flame_init, K x flame_step, flame_moments u,B,J -> pinned host, "
                   "flame_reduce scalars", "seconds": e2e_s, "gpu_launches": 1 + args.steps + 1 + 2,
