@@ -230,6 +230,7 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- accuracy
 ACC_STEPS = 50  # steps before the 256^3 fields are compared (chaos e-folds in ~20-25 steps)
+ACC_STEPS_LONG = 500  # the 256^3 configuration's run length: fields have decorrelated, spectra compare
 ORACLE_N, ORACLE_STEPS = 64, 100
 
 
@@ -418,23 +419,44 @@ def main():
     # fields are compared early, spectra by shell.
     acc_storages = [spec for spec in storages if "/" not in spec]
     accuracy = {st: {} for st in acc_storages}
-    finals = {}
-    for st in acc_storages:
-        sim = Flame(nx, ny, nz, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st, device=dev)
+    finals, longs = {}, {}
+    # control for the long comparison: FP16 storage with the one-site kernel,
+    # whose FP32 collision rounds in another order than the row kernel's
+    control = "fp16/site" if "fp16" in acc_storages else None
+    for st in acc_storages + ([control] if control else []):
+        st_storage, st_kernel = parse_variant(st)
+        sim = Flame(nx, ny, nz, w["tau_nu"], w["tau_eta"], w["d_i"], storage=st_storage, device=dev, kernel=st_kernel)
         sim.init(None, u_d, B_d)
         sim.step(ACC_STEPS)
         m = sim.moments(out={"u": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
                              "B": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)})
         Eu, Eb = sim.spectra(nshell)
         finals[st] = (m["u"], m["B"], Eu, Eb)
+        sim.step(ACC_STEPS_LONG - ACC_STEPS)
+        try:
+            sim.sync()
+            m = sim.moments(out={"u": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
+                                 "B": torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)})
+            Eu, Eb = sim.spectra(nshell)
+            longs[st] = (m["u"], m["B"], Eu, Eb)
+        except FlameError:
+            longs[st] = None  # non-finite by then: reported as such
         sim.close()
         del sim
     if "fp32" in finals:
-        ru, rb, rEu, rEb = finals["fp32"]
         for st in acc_storages:
             if st != "fp32":
                 accuracy[st]["vs_fp32_256"] = field_errors(finals[st], finals["fp32"], nmin, ACC_STEPS)
+                if longs.get(st) is not None and longs.get("fp32") is not None:
+                    accuracy[st]["vs_fp32_256_long"] = field_errors(longs[st], longs["fp32"], nmin, ACC_STEPS_LONG)
+                else:
+                    accuracy[st]["vs_fp32_256_long"] = {"steps": ACC_STEPS_LONG, "nonfinite": True}
+    if control and longs.get("fp16") is not None and longs.get(control) is not None:
+        accuracy["fp16"]["rounding_order_control_256_long"] = dict(
+            field_errors(longs["fp16"], longs[control], nmin, ACC_STEPS_LONG),
+            reference="FP16 storage, one-site kernel: the same step with the FP32 operations in another order")
     finals.clear()
+    longs.clear()
     torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: H2D of the initial
