@@ -96,12 +96,14 @@ typedef struct {
                          (removes launch overhead on small lattices)                    */
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
-    int kernel;       /* 0: automatic -- FLAME_SCHEME with FP16/BF16 storage, 64 <= nx <=
-                         512, nx a multiple of 64 and a 16-byte aligned state uses the
-                         row kernel (x rows staged in shared memory by TMA, two sites
-                         per thread in packed FP32 pairs), everything else the one-site
-                         kernel; 1: always the one-site kernel.  Both compute the same
-                         step in FP32; results agree to FP32 rounding before encoding. */
+    int kernel;       /* 0: automatic -- FLAME_SCHEME with FP16/BF16 storage, nx a
+                         multiple of 64 in 64..512 except 384 or in 960..1024 (the row
+                         lengths where it was timed faster) and a 16-byte aligned state
+                         use the row kernel (x rows staged in shared memory by TMA, two
+                         sites per thread in packed FP32 pairs), everything else the
+                         one-site kernel; 1: always the one-site kernel.  Both compute
+                         the same step in FP32; results agree to FP32 rounding before
+                         encoding. */
 } flame_params;
 
 typedef struct {
@@ -274,8 +276,8 @@ flame_status flame_reduce_static(flame_ctx *ctx, int nblocks, double *d_scalars)
  * `tries` polls per wait, synchronises, and returns FLAME_ERR_TIMEOUT
  * (sticky, like any failure); the state and the step count are left as they
  * were.  Errors: FLAME_ERR_PARAM (tries == 0, or the context does not run
- * the row kernel: FP16/BF16 storage, FLAME_SCHEME, kernel = 0, 64 <= nx <=
- * 512 with nx a multiple of 64), FLAME_ERR_STATE (before flame_init). */
+ * the row kernel: FP16/BF16 storage, FLAME_SCHEME, kernel = 0, nx as listed
+ * at flame_params.kernel), FLAME_ERR_STATE (before flame_init). */
 flame_status flame_debug_stall_next_step(flame_ctx *ctx, unsigned tries);
 
 /* Release the context and its internal workspace (not the caller's state). */

@@ -21,10 +21,11 @@
 //    0 writes the tile back with TMA stores to the rows it was loaded from.
 //  - The packed arithmetic halves the FP32 instruction count per site,
 //    which is what limited the one-site kernel with 16-bit storage.
-// Requirements: 16-bit storage, the paper's scheme, 64 <= nx <= 512 with nx
+// Requirements: 16-bit storage, the paper's scheme, 64 <= nx <= 1024 with nx
 // a multiple of 64 (row copies of whole 16-byte units, a whole number of
-// warps), a 16-byte aligned state.  Rows longer than 256 sites are moved by
-// one bulk copy per storage slot instead of tensor-map boxes.
+// warps), a 16-byte aligned state; flame_step uses it for the row lengths
+// where it is faster (row_kernel_wins).  Rows longer than 256 sites are moved
+// by one bulk copy per storage slot instead of tensor-map boxes.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -272,10 +273,9 @@ __device__ __forceinline__ void collide_pair(const LdF& ldf, const LdG& ldg, con
 }
 
 // ------------------------------------------- rows staged by TMA, persistent
-// At most 256 threads per block (nx <= 512); launch bounds per instantiation
+// At most 512 threads per block (nx <= 1024); launch bounds per instantiation
 // (row_bound_threads / row_bound_blocks below); stages: row_stages().
-constexpr int kRowMaxThreads = 256;
-constexpr int kRowMinBlocks = 2;
+constexpr int kRowMaxThreads = 512;
 // Rows up to this length are staged by tensor-map copies (a box is at most
 // 256 elements wide), longer ones by one bulk copy per row.
 constexpr int kBoxMaxX = 256;
@@ -468,12 +468,13 @@ struct RowIO {
   }
 };
 
-// Launch bounds per instantiation: a 256-site row (128 threads) with three
-// stages fits three blocks per SM by shared memory, so it may use up to 168
-// registers per thread at no cost in occupancy; the others stay at 128.
+// Launch bounds per instantiation: 128 registers per thread (512 threads'
+// worth per SM), except a 256-site row (128 threads) with three stages,
+// which fits three blocks per SM by shared memory and so may use up to 168
+// registers per thread at no cost in occupancy.
 constexpr int row_bound_threads(int nx) { return nx ? nx / 2 : kRowMaxThreads; }
 constexpr int row_bound_blocks(int nx, int stages) {
-  return nx == 256 && stages == 3 ? 3 : kRowMinBlocks * kRowMaxThreads / row_bound_threads(nx);
+  return nx == 256 && stages == 3 ? 3 : 512 / row_bound_threads(nx);
 }
 
 template <class T, bool ODD, int NX, int kRowStages>
@@ -667,9 +668,18 @@ cudaError_t row_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fla
 
 }  // namespace
 
+// Row lengths where the row kernel beats the one-site kernel.  Timed with
+// FP16 storage on 4M-site lattices (GLUPS, row / one-site): 64 26.6 / 23.8,
+// 128 29.8 / 23.9, 192 29.0 / 23.3, 256 30.7 / 23.9, 320 25.2 / 21.1, 384
+// 21.6 / 22.6, 448 24.3 / 22.6, 512 27.7 / 23.9, 576-832 16.9-20.6 /
+// 20.9-23.0, 896 21.6 / 21.6, 960 23.2 / 21.7, 1024 24.6 / 22.3.  Where it
+// loses, one or two blocks per SM leave 9-13 warps (shared memory and
+// registers per block grow with the row).
+bool row_kernel_wins(int nx) { return (nx <= 512 && nx != 384) || nx >= 960; }
+
 bool step_row_supported(Grid g, int storage, int variant, const void* pop) {
   return variant == kVarFlame && (storage == 2 || storage == 3) && g.nx >= 64 && g.nx <= 2 * kRowMaxThreads &&
-         g.nx % 64 == 0 && (reinterpret_cast<uintptr_t>(pop) & 15u) == 0;
+         g.nx % 64 == 0 && row_kernel_wins(g.nx) && (reinterpret_cast<uintptr_t>(pop) & 15u) == 0;
 }
 
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,

@@ -10,9 +10,10 @@ from gpu_helpers import rel_l2, run_both, turbulence
 pytestmark = pytest.mark.gpu
 
 # (nz, ny, nx): compile-time row lengths 64, 128, 256 and 512 and the general
-# one (192); single-row and single-plane lattices, where a row's periodic
-# y / z neighbours are the row itself
-SHAPES = [(6, 5, 64), (4, 3, 128), (3, 4, 192), (2, 3, 512), (1, 1, 64), (1, 2, 256)]
+# one (192, and 960 / 1024 with 480- / 512-thread blocks); single-row and
+# single-plane lattices, where a row's periodic y / z neighbours are the row
+# itself
+SHAPES = [(6, 5, 64), (4, 3, 128), (3, 4, 192), (2, 3, 512), (1, 1, 64), (1, 2, 256), (2, 1, 960), (1, 2, 1024)]
 B0 = np.array([0.0, 0.02, 0.05])
 
 
