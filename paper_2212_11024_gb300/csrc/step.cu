@@ -1,5 +1,8 @@
-// step.cu -- the fused FLAME collide-and-stream step: one thread per site,
-// AA in-place streaming over the 48-slot population state.
+// step.cu -- the fused FLAME collide-and-stream step, one thread per site,
+// AA in-place streaming over the 48-slot population state: the kernel for
+// FP32 storage, the scheme variants, and 16-bit storage where the row kernel
+// of step_row.cu (the same algebra, two sites per thread) does not apply.
+// launch_step chooses between the two.
 //
 // Algebra of the fluid collision.  With S = diag[1,1,1,1,w,w,w,w,w,1,...,1]
 // (eq. collision_matrix) every central moment except the five deviatoric
