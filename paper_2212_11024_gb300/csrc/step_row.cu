@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "aa.cuh"
 
@@ -567,31 +568,41 @@ size_t row_smem_bytes(int nx, size_t elem, int stages) {
 // one block per SM (30.1 against 17.5 at 512^3).
 constexpr int row_stages(int nx) { return nx > 128 && nx <= 256 ? 3 : 2; }
 
-// Launch configuration of one instantiation, cached: the shared-memory
-// opt-in and the resident blocks per SM (a function of nx only).
+// Launch configuration of one instantiation, cached per device (the
+// shared-memory opt-in and the resident blocks per SM depend on the device
+// and on nx only); a mutex makes concurrent host threads safe.
+constexpr int kMaxDevices = 64;
+
 template <class T, bool ODD, int NX, int S>
 cudaError_t row_config(const Grid& g, int* grid, size_t* smem_out) {
   auto kern = step_row_kernel<T, ODD, NX, S>;
   const int threads = g.nx / 2;
   const size_t smem = row_smem_bytes(g.nx, sizeof(T), S);
-  static size_t attr_smem = 0, occ_smem = 0;
-  static int occ = 0;
-  cudaError_t e;
-  if (smem > attr_smem) {
+  struct Cache {
+    size_t attr_smem, occ_smem;
+    int occ, nsm;
+  };
+  static Cache cache[kMaxDevices];
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  Cache& c = cache[dev];
+  if (smem > c.attr_smem) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    attr_smem = smem;
+    c.attr_smem = smem;
   }
-  if (smem != occ_smem) {
+  if (smem != c.occ_smem) {
     int per = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem)) != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
-    occ = per;
-    occ_smem = smem;
+    c.occ = per;
+    c.occ_smem = smem;
   }
-  int dev = 0, nsm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const long long ntiles = (long long)g.ny * g.nz, slots = (long long)occ * nsm;
+  if (c.nsm == 0 && (e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const long long ntiles = (long long)g.ny * g.nz, slots = (long long)c.occ * c.nsm;
   *grid = (int)(ntiles < slots ? ntiles : slots);
   *smem_out = smem;
   return cudaSuccess;
@@ -608,14 +619,16 @@ cudaError_t row_maps(const void* pop, const Grid& g, RowMaps* out) {
     *out = last;
     return cudaSuccess;
   }
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (thread-safe initialisation of a function-local static)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+    const cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    return e == cudaSuccess && q == cudaDriverEntryPointSuccess ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)
+                                                                : nullptr;
+  }();
+  if (!encode) return cudaErrorNotSupported;
   const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)kPop};
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 2, (cuuint64_t)g.nx * g.ny * 2, (cuuint64_t)g.n3 * 2};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
