@@ -486,6 +486,7 @@ def main():
     sim.step(args.steps)
     mark()
     sim.moments(out=outs)
+    mark()
     out_h[0:3].copy_(outs["u"], non_blocking=True)
     out_h[3:6].copy_(outs["B"], non_blocking=True)
     out_h[6:9].copy_(outs["J"], non_blocking=True)
@@ -506,7 +507,7 @@ def main():
                   "flame_reduce scalars", "seconds": e2e_s, "gpu_launches": 1 + args.steps + 1 + 2,
            "final_E_u": scal["E_u"], "final_E_B": scal["E_B"],
            "phases_ms": {k: (marks[i + 1] - marks[i]) * 1e3 for i, k in
-                         enumerate(("h2d", "init", "steps", "moments_d2h", "reduce"))},
+                         enumerate(("h2d", "init", "steps", "moments", "d2h", "reduce"))},
            "sm_mhz": e2e_sm}
     clk = clocks.stop()
 
