@@ -72,7 +72,7 @@ def kernel_source_hash():
     and whitespace removed, so that only a change of the code itself
     invalidates a recorded ncu traffic figure."""
     h = hashlib.sha256()
-    for f in ("step.cu", "step_row.cu", "lattice.cuh", "aa.cuh"):
+    for f in ("step.cu", "step_row.cu", "step_row.cuh", "lattice.cuh", "aa.cuh"):
         with open(os.path.join(ROOT, "paper_2212_11024_gb300", "csrc", f)) as fh:
             txt = fh.read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)

@@ -278,7 +278,7 @@ flame_status flame_step(flame_ctx* c, int n) {
     // The wait-failure test: one launch whose waits all run out; it leaves
     // the state as it was, so step and parity do not advance.
     cudaError_t e = flame::launch_step_row(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream,
-                                           c->stall_tries);
+                                           c->p.variant, c->d_bfield, c->stall_tries);
     c->stall_tries = 0;
     if (e != cudaSuccess) return cuda_fail(c, e);
     return sync_and_check(c);

@@ -36,18 +36,24 @@ cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConst
 
 // The step for 16-bit storage as a persistent kernel over x rows staged in
 // shared memory by TMA, two sites per thread in packed FP32 pairs
-// (step_row.cu): kVarFlame, 64 <= nx <= 1024 with nx a multiple of 64 where
-// the row kernel is the faster one (64-512 except 384, 960-1024), a
+// (step_row.cuh): every variant, 64 <= nx <= 1024 with nx a multiple of 64
+// where the row kernel is the faster one (64-512 except 384, 960-1024), a
 // 16-byte aligned state.  flag bit 1: a non-finite moment; bit 2: a staged
 // copy did not complete within the wait limit.
 bool step_row_supported(Grid g, int storage, int variant, const void* pop);
 // Settles the launch configuration of the kernel launch_step would use
 // (no launch); needed once before stream capture.
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel);
-// stall_tries > 0: the failure-path test -- the launch arms its barriers
-// without issuing copies and gives up after stall_tries polls per wait.
+// Bfd: the pre-collision B - B_ref (3 N3 floats) that launch_bfield wrote,
+// read by kVarFdCurrent only.  stall_tries > 0: the failure-path test -- the
+// launch arms its barriers without issuing copies and gives up after
+// stall_tries polls per wait.
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                            cudaStream_t s, unsigned stall_tries = 0);
+                            cudaStream_t s, int variant = kVarFlame, const float* Bfd = nullptr,
+                            unsigned stall_tries = 0);
+// The pre-pass of kVarFdCurrent: B - B_ref of the pre-collision populations
+// at every site into Bfd (FP32, [3][N3]).
+cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, float* Bfd, cudaStream_t s);
 
 cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
                         const double* u, const double* B, const double* gu, const double* gB,

@@ -1,8 +1,9 @@
 // step.cu -- the fused FLAME collide-and-stream step, one thread per site,
 // AA in-place streaming over the 48-slot population state: the kernel for
-// FP32 storage, the scheme variants, and 16-bit storage where the row kernel
-// of step_row.cu (the same algebra, two sites per thread) does not apply.
-// launch_step chooses between the two.
+// FP32 storage, and for 16-bit storage where the row kernel of step_row.cuh
+// (the same algebra and variants, two sites per thread) does not apply.
+// launch_step chooses between the two; the finite-difference current's B
+// pre-pass (bfield_kernel) serves both.
 //
 // Algebra of the fluid collision.  With S = diag[1,1,1,1,w,w,w,w,w,1,...,1]
 // (eq. collision_matrix) every central moment except the five deviatoric
@@ -291,6 +292,17 @@ __global__ void bfield_kernel(Slots<T> P, Grid g, float* __restrict__ Bfd) {
   }
 }
 
+template <class T>
+cudaError_t bfield_t(int odd, const void* pop, Grid g, float* Bfd, cudaStream_t s) {
+  const dim3 bb = site_block(g, 128), gb = site_grid(g, bb);
+  const Slots<T> P = make_slots<T>(pop, g);
+  if (odd)
+    bfield_kernel<T, true><<<gb, bb, 0, s>>>(P, g, Bfd);
+  else
+    bfield_kernel<T, false><<<gb, bb, 0, s>>>(P, g, Bfd);
+  return cudaGetLastError();
+}
+
 template <class T, int VAR>
 void step_launch(int odd, const Slots<T>& P, Grid g, const StepConsts& k, unsigned* flag, const float* Bfd, dim3 gr,
                  dim3 b, cudaStream_t s) {
@@ -311,11 +323,8 @@ cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fl
     case kVarEmhd: step_launch<T, kVarEmhd>(odd, P, g, k, flag, nullptr, gr, b, s); break;
     case kVarFdCurrent: {
       if (!Bfd) return cudaErrorInvalidValue;
-      const dim3 bb = site_block(g, 128), gb = site_grid(g, bb);
-      if (odd)
-        bfield_kernel<T, true><<<gb, bb, 0, s>>>(P, g, Bfd);
-      else
-        bfield_kernel<T, false><<<gb, bb, 0, s>>>(P, g, Bfd);
+      const cudaError_t e = bfield_t<T>(odd, pop, g, Bfd, s);
+      if (e != cudaSuccess) return e;
       step_launch<T, kVarFdCurrent>(odd, P, g, k, flag, Bfd, gr, b, s);
       break;
     }
@@ -327,10 +336,25 @@ cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fl
 
 }  // namespace
 
+cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, float* Bfd, cudaStream_t s) {
+  if (!Bfd) return cudaErrorInvalidValue;
+  switch (storage) {
+    case 1: return bfield_t<float>(odd, pop, g, Bfd, s);
+    case 2: return bfield_t<__half>(odd, pop, g, Bfd, s);
+    case 3: return bfield_t<__nv_bfloat16>(odd, pop, g, Bfd, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
                         cudaStream_t s, int variant, float* Bfd, int kernel) {
-  if (kernel == 0 && step_row_supported(g, storage, variant, pop))
-    return launch_step_row(storage, odd, pop, g, k, flag, s);
+  if (kernel == 0 && step_row_supported(g, storage, variant, pop)) {
+    if (variant == kVarFdCurrent) {
+      const cudaError_t e = launch_bfield(storage, odd, pop, g, Bfd, s);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_step_row(storage, odd, pop, g, k, flag, s, variant, Bfd);
+  }
   switch (storage) {
     case 1: return step_t<float>(odd, pop, g, k, flag, variant, Bfd, s);
     case 2: return step_t<__half>(odd, pop, g, k, flag, variant, Bfd, s);

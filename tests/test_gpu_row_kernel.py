@@ -1,11 +1,14 @@
 """The row kernel for 16-bit storage (x rows staged in shared memory by TMA,
 two sites per thread in packed FP32 pairs) against the FP64 oracle and
-against the one-site kernel.  Row lengths 64, 128 and 512 take the
-compile-time row length instantiations, 192 the general one."""
+against the one-site kernel, for the paper's scheme and its variants (BGK
+fluid, electron MHD, finite-difference current).  Row lengths 64, 128, 256
+and 512 take the compile-time row length instantiations, 192, 960 and 1024
+the general one."""
 import numpy as np
 import pytest
 
-from gpu_helpers import rel_l2, run_both, turbulence
+import oracle as O
+from gpu_helpers import rel_dev_err, rel_l2, rest_populations, run_both, turbulence
 
 pytestmark = pytest.mark.gpu
 
@@ -127,3 +130,78 @@ def test_row_kernel_wait_limit_reports_timeout():
     assert torch.equal(a.populations(), b.populations())
     a.close()
     b.close()
+
+
+# the variants on compile-time (64, 256) and general (192, 960: bulk row
+# copies) row lengths, including a single-row lattice
+VARIANT_SHAPES = [(6, 5, 64), (3, 4, 192), (2, 3, 256), (2, 1, 960), (1, 1, 64)]
+
+
+def _variant_run(shape, storage, kernel, variant, steps, seed):
+    from paper_2212_11024_gb300 import Flame
+    nz, ny, nx = shape
+    u, B = _fields(shape, seed)
+    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), kernel=kernel, variant=variant)
+    sim.init(None, u, B)
+    sim.step(steps)
+    f = sim.populations().cpu().numpy()
+    m = {k: v.cpu().numpy() for k, v in sim.moments().items()}
+    assert sim.sync() is None
+    sim.close()
+    return u, B, f, m
+
+
+@pytest.mark.parametrize("shape", VARIANT_SHAPES)
+@pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-2), ("bf16", 1e-1)])
+def test_row_kernel_variants_vs_oracle(shape, variant, storage, tol):
+    """21 steps of each variant with 16-bit storage on the row kernel against
+    the oracle's variant: relative L2 of the population deviations (fluid and
+    magnetic) and of the u and B fluctuations."""
+    nz, ny, nx = shape
+    u, B, fg, mg = _variant_run(shape, storage, "auto", variant, 21, 51)
+    p = O.Params(nx, ny, nz, 0.52, 0.55, 1.5)
+    fo = O.init(p, None, u, B)
+    O.step_variant(p, fo, 21, variant, literal=False)
+    mo = O.moments(p, fo)
+    rest = rest_populations(shape, 1.0, tuple(B0))
+    assert rel_dev_err(fg, fo, rest, slice(0, 27)) < tol
+    assert rel_dev_err(fg, fo, rest, slice(27, 48)) < tol
+    b0 = B0[:, None, None, None]
+    assert rel_l2(mg["u"], mo["u"]) < tol
+    assert rel_l2(mg["B"] - b0, mo["B"] - b0) < tol
+
+
+@pytest.mark.parametrize("shape", VARIANT_SHAPES)
+@pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
+def test_row_kernel_variants_agree_with_site_kernel(shape, variant):
+    """FP16, 9 steps of each variant, row kernel vs one-site kernel: a few
+    half-precision units of the last place apart at most, and apart
+    somewhere (the row kernel ran)."""
+    pops = [_variant_run(shape, "fp16", kernel, variant, 9, 53)[2] for kernel in ("auto", "site")]
+    a, b = pops
+    dev = np.abs(b - np.median(b, axis=(1, 2, 3), keepdims=True)).max()
+    d = np.abs(a - b)
+    assert d.max() < 8 * 2.0 ** -11 * dev, d.max() / dev
+    assert (d > 0).any()
+    assert (d > 0).mean() < 0.5
+
+
+@pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
+def test_row_kernel_variant_graph_replay_is_bit_identical(variant):
+    """Graph replays of a variant's row-kernel steps (with the B pre-pass of
+    the finite-difference current in the graph) equal single launches."""
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    shape = (4, 3, 128)
+    nz, ny, nx = shape
+    u, B = _fields(shape, 55)
+    a = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="bf16", B_ref=tuple(B0), variant=variant)
+    b = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="bf16", B_ref=tuple(B0), variant=variant, graph_steps=8)
+    for s in (a, b):
+        s.init(None, u, B)
+    for n in (5, 19):
+        a.step(n)
+        b.step(n)
+    assert torch.equal(a.populations(), b.populations())
+    assert a.sync() is None and b.sync() is None
