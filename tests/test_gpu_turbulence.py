@@ -53,3 +53,13 @@ def test_decay_hall_fp16_tracks_fp32():
         ref = a[key][1]
         big = ref > 1e-4 * ref.max()
         assert np.allclose(b[key][1][big], ref[big], rtol=1e-2), key
+
+
+def test_step_throughput_reports_every_configuration():
+    """The throughput helper times a variant on either kernel and reports a
+    finite state."""
+    from paper_2212_11024_gb300.throughput import step_throughput
+    for variant, storage, kernel in (("bgk", "fp16", "auto"), ("fd_current", "bf16", "site"), ("emhd", "fp32", "site")):
+        r = step_throughput(64, variant, storage, kernel, steps=6, warmup=3, d_i=1.0, tau=0.6, graph_steps=2)
+        assert r["glups"] > 0 and r["nonfinite_sites"] == 0
+        assert r["state_bytes_per_update"] == (384 if storage == "fp32" else 192)
