@@ -96,7 +96,7 @@ typedef struct {
                          (removes launch overhead on small lattices)                    */
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
-    int kernel;       /* 0: automatic -- FLAME_SCHEME with FP16/BF16 storage, nx a
+    int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant), nx a
                          multiple of 64 in 64..512 except 384 or in 960..1024 (the row
                          lengths where it was timed faster) and a 16-byte aligned state
                          use the row kernel (x rows staged in shared memory by TMA, two

@@ -8,12 +8,14 @@ current obtained from the magnetic non-equilibrium moments.
 - ``Flame``   : ctypes binding of libflame.so (include/flame.h); CUDA only.
                 The step runs one of two kernels: the row kernel (FP16/BF16
                 storage: TMA-staged x rows, two sites per thread in packed
-                FP32) or the one-site kernel (FP32 storage, the variants).
+                FP32) or the one-site kernel (FP32 storage, and row lengths
+                the row kernel does not take); both run every variant.
 - ``inputs``  : seeded synthetic initial conditions (numpy).
 - ``units``   : lattice-unit parameter mapping and the whistler CFL check.
 - ``adjoint`` : gradients of a band magnetic energy through N steps
                 (FlameBandEnergy autograd Function, sqrt(N) checkpointing).
 - ``turbulence``: decaying-turbulence runs with spectra and step throughput.
+- ``throughput``: step throughput of any variant, storage and kernel.
 - ``budget``  : the wavenumber energy budget S(k), D(k) of Sec. 4.3 (torch.fft).
 - ``validation``: the Table 1 three-mode runs and the paper's error metrics.
 - ``build``   : nvcc build of libflame.so for sm_103a.
