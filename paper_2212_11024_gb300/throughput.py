@@ -13,6 +13,11 @@ timed steps (a run that went non-finite is still timed, but is flagged).
 
     python -m paper_2212_11024_gb300.throughput --n 256 --variants flame,bgk,emhd,fd_current \\
         --storage fp16,bf16,fp32 --kernels auto,site
+    python -m paper_2212_11024_gb300.throughput --n 256 --adjoint --storage fp32,fp16
+
+``--adjoint`` times flame_step_adjoint instead: one stored state, a seeded
+FP32 lambda_{t+1}, 576 B per update with FP32 storage (state read, lambda
+gathered and written), 480 with 16-bit storage.
 """
 from __future__ import annotations
 
@@ -58,6 +63,53 @@ def step_throughput(n, variant="flame", storage="fp16", kernel="auto", steps=200
                 nonfinite_sites=bad)
 
 
+def adjoint_throughput(n, storage="fp32", steps=30, warmup=3, d_i=None, tau=0.51, fields=None, device=None):
+    """Time ``steps`` calls of flame_step_adjoint on one stored state at n^3
+    (lambda_{t+1} seeded Gaussian, FP32): ms per call, GLUPS and the bytes per
+    update (state read, lambda_{t+1} gathered and lambda_t written: 48 values
+    each)."""
+    import ctypes
+
+    import torch
+
+    from .flame import _check, library
+
+    if fields is None:
+        u, B = inputs.turbulence((n, n, n), 3, 4, 0.05, 0.05, shells=(1, 4))
+    else:
+        u, B = fields
+    d_i = 0.05 * n if d_i is None else d_i
+    sim = Flame(n, n, n, tau, tau, d_i, storage=storage, device=device)
+    try:
+        sim.init(None, u, B)
+        sim.step(3)
+        blob, _, par = sim.get_state()
+        gen = torch.Generator(device=sim.device)
+        gen.manual_seed(7)
+        lam_in = torch.randn((48, n ** 3), dtype=torch.float32, device=sim.device, generator=gen)
+        lam_out = torch.empty_like(lam_in)
+        ddi = torch.zeros(1, dtype=torch.float64, device=sim.device)
+        lib = library()
+        args = (sim._ctx, ctypes.c_void_p(blob.data_ptr()), par, ctypes.c_void_p(lam_in.data_ptr()),
+                ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(ddi.data_ptr()))
+        for _ in range(warmup):
+            _check(lib.flame_step_adjoint(*args), "flame_step_adjoint")
+        stream = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(sim.device)
+        e0.record(stream)
+        for _ in range(steps):
+            _check(lib.flame_step_adjoint(*args), "flame_step_adjoint")
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        sim.close()
+    bpu = 48 * (STATE_BYTES[storage] // 96) + 2 * 48 * 4
+    return dict(n=n, kernel="adjoint_step", storage=storage, steps=steps, ms_per_step=ms,
+                glups=n ** 3 / (ms * 1e-3) / 1e9, bytes_per_update=bpu)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--n", type=int, default=256)
@@ -70,8 +122,17 @@ def main(argv=None):
     ap.add_argument("--tau", type=float, default=0.51)
     ap.add_argument("--peak-gbs", type=float, default=None,
                     help="HBM bandwidth to report the state traffic against (GB/s)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time flame_step_adjoint (per storage) instead of the forward step")
     a = ap.parse_args(argv)
     u, B = inputs.turbulence((a.n,) * 3, 3, 4, 0.05, 0.05, shells=(1, 4))
+    if a.adjoint:
+        for st in a.storage.split(","):
+            r = adjoint_throughput(a.n, st, min(a.steps, 100), a.warmup, a.d_i, a.tau, fields=(u, B))
+            if a.peak_gbs:
+                r["frac_of_peak"] = r["glups"] * r["bytes_per_update"] / a.peak_gbs
+            print(json.dumps(r), flush=True)
+        return
     for v in a.variants.split(","):
         for st in a.storage.split(","):
             # FP32 storage always runs the one-site kernel

@@ -63,3 +63,10 @@ def test_step_throughput_reports_every_configuration():
         r = step_throughput(64, variant, storage, kernel, steps=6, warmup=3, d_i=1.0, tau=0.6, graph_steps=2)
         assert r["glups"] > 0 and r["nonfinite_sites"] == 0
         assert r["state_bytes_per_update"] == (384 if storage == "fp32" else 192)
+
+
+def test_adjoint_throughput_reports_a_time():
+    from paper_2212_11024_gb300.throughput import adjoint_throughput
+    for storage in ("fp32", "bf16"):
+        r = adjoint_throughput(32, storage, steps=3, warmup=1)
+        assert r["glups"] > 0 and r["bytes_per_update"] == (576 if storage == "fp32" else 480)
