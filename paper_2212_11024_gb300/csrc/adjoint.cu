@@ -31,24 +31,25 @@
 namespace flame {
 namespace {
 
-// 128-thread blocks, three per SM: the step adjoint keeps the whole transposed
-// Jacobian of a site live (168 registers, no spills); 12 warps per SM ran
-// 33-42 % faster than one 256-thread block (185 registers, 8 warps) and than
-// 128-register bounds with spills (16 warps).
+// 128-thread blocks, four per SM (16 warps, 128 registers): the step adjoint
+// keeps much of a site's transposed Jacobian live and waits on its loads, so
+// warps pay more than the ~20 bytes of spills the bound costs (timed against
+// three blocks of 168 registers without spills: 6-13 % faster; against one
+// 256-thread block of 185 registers: 1.5x).
 constexpr int kAdjThreads = 128;
-constexpr int kAdjMinBlocks = 3;
+constexpr int kAdjMinBlocks = 4;
 
 // 1-D functions of the undivided equilibrium and inverse-moment maps, and
 // their derivatives in u, at velocity component c (index p = c + 1).
+// (The u derivative of F0 equals F1.)
 struct Axis {
-  float psi[3], dpsi[3], F0[3], F1[3], dF0[3];
+  float psi[3], dpsi[3], F0[3], F1[3];
   __device__ __forceinline__ explicit Axis(float u) {
     const float uu = u * u;
     psi[1] = 2.f / 3.f - uu;
     dpsi[1] = -2.f * u;
     F0[1] = 1.f - uu;
     F1[1] = -2.f * u;
-    dF0[1] = -2.f * u;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const float c = h == 0 ? -1.f : 1.f;
@@ -57,12 +58,54 @@ struct Axis {
       dpsi[p] = u + 0.5f * c;
       F0[p] = 0.5f * (uu + c * u);
       F1[p] = u + 0.5f * c;
-      dF0[p] = u + 0.5f * c;
     }
   }
 };
-__device__ __forceinline__ float F2(int p) { return p == 1 ? -1.f : 0.5f; }
-__device__ __forceinline__ float dF1(int p) { return p == 1 ? -2.f : 1.f; }
+
+// Separable sums over the velocity cube, sum_p t[pz][py][px] fx(px) fy(py)
+// fz(pz), as three 1-D passes (x, then y, then z), so that the partial sums
+// are shared between the many products the adjoint needs.  A 1-D function
+// of p = c + 1 is a table of values (Fv: the U-dependent factors) or one of
+// the constant tables (Fc) written out, so that their zero entries cost
+// nothing: F2 = (1/2, -1, 1/2) (the second-order inverse map), dF1 =
+// (1, -2, 1) (u derivative of F1), the 1-D weights w = (1/6, 2/3, 1/6), w c,
+// w c^2, and (1, 4, 1), c, c^2 (moments of the 216-scaled weights).
+enum : int { kFnF2, kFnDF1, kFnW, kFnWC, kFnWC2, kFnM0, kFnM1, kFnM2 };
+template <int K>
+struct Fc {};
+struct Fv {
+  const float* f;
+};
+__device__ __forceinline__ float app(Fv F, float a0, float a1, float a2) {
+  return fmaf(a2, F.f[2], fmaf(a1, F.f[1], a0 * F.f[0]));
+}
+template <int K>
+__device__ __forceinline__ float app(Fc<K>, float a0, float a1, float a2) {
+  if constexpr (K == kFnF2) return fmaf(0.5f, a0 + a2, -a1);
+  else if constexpr (K == kFnDF1) return fmaf(-2.f, a1, a0 + a2);
+  else if constexpr (K == kFnW) return fmaf(2.f / 3.f, a1, (1.f / 6.f) * (a0 + a2));
+  else if constexpr (K == kFnWC) return (1.f / 6.f) * (a2 - a0);
+  else if constexpr (K == kFnWC2) return (1.f / 6.f) * (a0 + a2);
+  else if constexpr (K == kFnM0) return fmaf(4.f, a1, a0 + a2);
+  else if constexpr (K == kFnM1) return a2 - a0;
+  else return a0 + a2;
+}
+template <class F>
+__device__ __forceinline__ void xpass(const float (&t)[3][3][3], F f, float (&o)[3][3]) {
+#pragma unroll
+  for (int pz = 0; pz < 3; ++pz)
+#pragma unroll
+    for (int py = 0; py < 3; ++py) o[pz][py] = app(f, t[pz][py][0], t[pz][py][1], t[pz][py][2]);
+}
+template <class F>
+__device__ __forceinline__ void ypass(const float (&x)[3][3], F f, float (&o)[3]) {
+#pragma unroll
+  for (int pz = 0; pz < 3; ++pz) o[pz] = app(f, x[pz][0], x[pz][1], x[pz][2]);
+}
+template <class F>
+__device__ __forceinline__ float zpass(const float (&y)[3], F f) {
+  return app(f, y[0], y[1], y[2]);
+}
 
 __device__ __forceinline__ void block_sum_to(double v, double* out) {
   __shared__ double sh[32];
@@ -105,21 +148,36 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
 #pragma unroll
       for (int i = 0; i < kM; ++i)
         sg[b][i] = Codec<T>::dec(P.p[mslot(b, ODD ? opp7(i) : i)][site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i))]);
-    float drho = 0.f, jv[3] = {0.f, 0.f, 0.f}, pv[3][3] = {{0.f}};
+    // sums of 216 w_i f_i times 1, c_a and c_a c_b, by 1-D passes with (1, 4, 1)
+    float drho, jv[3], pv[3][3];
+    {
+      float tc[3][3][3];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const float t = (float)w27x216(i) * sf[i];
-      const int c[3] = {cx27(i), cy27(i), cz27(i)};
-      drho += t;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (c[a] != 0) jv[a] += c[a] > 0 ? t : -t;
-#pragma unroll
-        for (int b = a; b < 3; ++b)
-          if (c[a] * c[b] != 0) pv[a][b] += c[a] * c[b] > 0 ? t : -t;
-      }
+      for (int i = 0; i < kQ; ++i) tc[cz27(i) + 1][cy27(i) + 1][cx27(i) + 1] = sf[i];
+      const Fc<kFnM0> m0;
+      const Fc<kFnM1> m1;
+      const Fc<kFnM2> m2;
+      float X0[3][3], X1[3][3], X2[3][3], Y[3];
+      xpass(tc, m0, X0);
+      xpass(tc, m1, X1);
+      xpass(tc, m2, X2);
+      ypass(X0, m0, Y);
+      drho = zpass(Y, m0) / 216.f;
+      jv[2] = zpass(Y, m1);
+      pv[2][2] = zpass(Y, m2);
+      ypass(X0, m1, Y);
+      jv[1] = zpass(Y, m0);
+      pv[1][2] = zpass(Y, m1);
+      ypass(X0, m2, Y);
+      pv[1][1] = zpass(Y, m0);
+      ypass(X1, m0, Y);
+      jv[0] = zpass(Y, m0);
+      pv[0][2] = zpass(Y, m1);
+      ypass(X1, m1, Y);
+      pv[0][1] = zpass(Y, m0);
+      ypass(X2, m0, Y);
+      pv[0][0] = zpass(Y, m0);
     }
-    drho /= 216.f;
     const float rho = k.rho0 + drho;
     const float U[3] = {jv[0] / (216.f * rho), jv[1] / (216.f * rho), jv[2] / (216.f * rho)};
     float dB[3], lam[3][3];
@@ -247,45 +305,93 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
       Lb[1][0] = -Ab[2];
     }
 
-    // ---- fluid collision: contractions of fbar* = lf
+    // ---- fluid collision: contractions of fbar* = lf with products of 1-D
+    // functions (grouped by the x function, 1-D passes)
     const Axis ax(U[0]), ay(U[1]), az(U[2]);
     const float Dxx = D[0][0], Dyy = D[1][1], Dzz = D[2][2], Dxy = D[0][1], Dxz = D[0][2], Dyz = D[1][2];
-    float rb = 0.f, Ueq[3] = {0.f, 0.f, 0.f}, UP[3] = {0.f, 0.f, 0.f};
-    float Dbxx = 0.f, Dbyy = 0.f, Dbzz = 0.f, Dbxy = 0.f, Dbxz = 0.f, Dbyz = 0.f;
-    float r0 = 0.f, R[3][3] = {{0.f}};
+    float rb, Ueq[3], UP[3] = {0.f, 0.f, 0.f};
+    float Dbxx, Dbyy, Dbzz, Dbxy, Dbxz, Dbyz;
+    float r0, R[3][3];
+    {
+      float tl[3][3][3];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const int px = cx27(i) + 1, py = cy27(i) + 1, pz = cz27(i) + 1;
-      const float t = lf[i];
-      const float pxy = ax.psi[px] * ay.psi[py];
-      rb += t * pxy * az.psi[pz];
-      Ueq[0] += t * ax.dpsi[px] * ay.psi[py] * az.psi[pz];
-      Ueq[1] += t * ax.psi[px] * ay.dpsi[py] * az.psi[pz];
-      Ueq[2] += t * pxy * az.dpsi[pz];
-      const float f0x = ax.F0[px], f0y = ay.F0[py], f0z = az.F0[pz];
-      const float f1x = ax.F1[px], f1y = ay.F1[py], f1z = az.F1[pz];
-      const float f2x = F2(px), f2y = F2(py), f2z = F2(pz);
-      Dbxx += t * f2x * f0y * f0z;
-      Dbyy += t * f0x * f2y * f0z;
-      Dbzz += t * f0x * f0y * f2z;
-      Dbxy += t * f1x * f1y * f0z;
-      Dbxz += t * f1x * f0y * f1z;
-      Dbyz += t * f0x * f1y * f1z;
-      // derivative of P in U_a: only the a-axis factor is differentiated
-      UP[0] += t * (ax.dF0[px] * (Dyy * f2y * f0z + Dzz * f0y * f2z + Dyz * f1y * f1z) +
-                    dF1(px) * (Dxy * f1y * f0z + Dxz * f0y * f1z));
-      UP[1] += t * (ay.dF0[py] * (Dxx * f2x * f0z + Dzz * f0x * f2z + Dxz * f1x * f1z) +
-                    dF1(py) * (Dxy * f1x * f0z + Dyz * f0x * f1z));
-      UP[2] += t * (az.dF0[pz] * (Dxx * f2x * f0y + Dyy * f0x * f2y + Dxy * f1x * f1y) +
-                    dF1(pz) * (Dxz * f1x * f0y + Dyz * f0x * f1y));
-      const float wt = (float)w27d(i) * t;
-      const int c[3] = {px - 1, py - 1, pz - 1};
-      r0 += wt;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = a; b < 3; ++b)
-          if (c[a] * c[b] != 0) R[a][b] += c[a] * c[b] > 0 ? wt : -wt;
+      for (int i = 0; i < kQ; ++i) tl[cz27(i) + 1][cy27(i) + 1][cx27(i) + 1] = lf[i];
+      const Fv Px{ax.psi}, Py{ay.psi}, Pz{az.psi}, DPx{ax.dpsi}, DPy{ay.dpsi}, DPz{az.dpsi};
+      const Fv F0x{ax.F0}, F0y{ay.F0}, F0z{az.F0}, F1x{ax.F1}, F1y{ay.F1}, F1z{az.F1};
+      const Fc<kFnF2> F2c;
+      const Fc<kFnDF1> dF1c;
+      const Fc<kFnW> Wc;
+      const Fc<kFnWC> WCc;
+      const Fc<kFnWC2> WC2c;
+      float X[3][3], Y[3];
+      // equilibrium: rho prod psi and its U derivatives
+      xpass(tl, Px, X);
+      ypass(X, Py, Y);
+      rb = zpass(Y, Pz);
+      Ueq[2] = zpass(Y, DPz);
+      ypass(X, DPy, Y);
+      Ueq[1] = zpass(Y, Pz);
+      xpass(tl, DPx, X);
+      ypass(X, Py, Y);
+      Ueq[0] = zpass(Y, Pz);
+      // P(D, U): Dbar and the U derivatives (dF0 = F1)
+      xpass(tl, F0x, X);
+      ypass(X, F2c, Y);
+      Dbyy = zpass(Y, F0z);
+      UP[2] = fmaf(Dyy, zpass(Y, F1z), UP[2]);
+      ypass(X, F0y, Y);
+      Dbzz = zpass(Y, F2c);
+      ypass(X, F1y, Y);
+      Dbyz = zpass(Y, F1z);
+      UP[1] = fmaf(Dzz, zpass(Y, F2c), UP[1]);
+      UP[2] = fmaf(Dyz, zpass(Y, dF1c), UP[2]);
+      ypass(X, dF1c, Y);
+      UP[1] = fmaf(Dyz, zpass(Y, F1z), UP[1]);
+      xpass(tl, F1x, X);
+      ypass(X, F1y, Y);
+      Dbxy = zpass(Y, F0z);
+      {
+        const float t111 = zpass(Y, F1z);
+        UP[0] = fmaf(Dyz, t111, UP[0]);
+        UP[1] = fmaf(Dxz, t111, UP[1]);
+        UP[2] = fmaf(Dxy, t111, UP[2]);
+      }
+      ypass(X, F0y, Y);
+      Dbxz = zpass(Y, F1z);
+      UP[0] = fmaf(Dzz, zpass(Y, F2c), UP[0]);
+      UP[2] = fmaf(Dxz, zpass(Y, dF1c), UP[2]);
+      ypass(X, F2c, Y);
+      UP[0] = fmaf(Dyy, zpass(Y, F0z), UP[0]);
+      ypass(X, dF1c, Y);
+      UP[1] = fmaf(Dxy, zpass(Y, F0z), UP[1]);
+      xpass(tl, F2c, X);
+      ypass(X, F0y, Y);
+      Dbxx = zpass(Y, F0z);
+      UP[2] = fmaf(Dxx, zpass(Y, F1z), UP[2]);
+      ypass(X, F1y, Y);
+      UP[1] = fmaf(Dxx, zpass(Y, F0z), UP[1]);
+      xpass(tl, dF1c, X);
+      ypass(X, F1y, Y);
+      UP[0] = fmaf(Dxy, zpass(Y, F0z), UP[0]);
+      ypass(X, F0y, Y);
+      UP[0] = fmaf(Dxz, zpass(Y, F1z), UP[0]);
+      // Lorentz term: r0 = sum w_i fbar_i, R_ab = sum w_i fbar_i c_a c_b
+      xpass(tl, Wc, X);
+      ypass(X, Wc, Y);
+      r0 = zpass(Y, Wc);
+      R[2][2] = zpass(Y, WC2c);
+      ypass(X, WC2c, Y);
+      R[1][1] = zpass(Y, Wc);
+      ypass(X, WCc, Y);
+      R[1][2] = zpass(Y, WCc);
+      xpass(tl, WC2c, X);
+      ypass(X, Wc, Y);
+      R[0][0] = zpass(Y, Wc);
+      xpass(tl, WCc, X);
+      ypass(X, WCc, Y);
+      R[0][1] = zpass(Y, Wc);
+      ypass(X, Wc, Y);
+      R[0][2] = zpass(Y, WCc);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) Ub[a] += rho * Ueq[a] + UP[a];
@@ -327,20 +433,28 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
     const float jb[3] = {Ub[0] / rho, Ub[1] / rho, Ub[2] / rho};
     rb -= (Ub[0] * U[0] + Ub[1] * U[1] + Ub[2] * U[2]) / rho;
 
-    // ---- moments -> populations
+    // ---- moments -> populations: fbar_i = rhobar + jbar.c_i + Pibar : c_i c_i,
+    // per (c_x, c_y) column as base + lin c_z + Pibar_zz c_z^2
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      const int c[3] = {cx27(i), cy27(i), cz27(i)};
-      float v = rb;
+    for (int py = 0; py < 3; ++py)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (c[a] != 0) v += c[a] > 0 ? jb[a] : -jb[a];
-#pragma unroll
-        for (int b = a; b < 3; ++b)
-          if (c[a] * c[b] != 0) v += c[a] * c[b] > 0 ? Sb[a][b] : -Sb[a][b];
+      for (int px = 0; px < 3; ++px) {
+        const int cx = px - 1, cy = py - 1;
+        float base = rb, lin = jb[2];
+        if (cx != 0) {
+          base += (cx > 0 ? jb[0] : -jb[0]) + Sb[0][0];
+          lin += cx > 0 ? Sb[0][2] : -Sb[0][2];
+        }
+        if (cy != 0) {
+          base += (cy > 0 ? jb[1] : -jb[1]) + Sb[1][1];
+          lin += cy > 0 ? Sb[1][2] : -Sb[1][2];
+        }
+        if (cx * cy != 0) base += cx * cy > 0 ? Sb[0][1] : -Sb[0][1];
+        const float side = base + Sb[2][2];
+        lam_out[(long long)idx27(px, py, 0) * n3 + site] = side - lin;
+        lam_out[(long long)idx27(px, py, 1) * n3 + site] = base;
+        lam_out[(long long)idx27(px, py, 2) * n3 + site] = side + lin;
       }
-      lam_out[(long long)i * n3 + site] = v;
-    }
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
