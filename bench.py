@@ -419,6 +419,18 @@ def main():
         del sim
         torch.cuda.empty_cache()
 
+    # The hand-written adjoint step (flame_step_adjoint, the differentiation
+    # path) on the same workload, outside the headline: 20 calls after 3.
+    adjoint = {}
+    if nx == ny == nz:
+        from paper_2212_11024_gb300.throughput import adjoint_throughput
+        for st in ("fp32", "fp16"):
+            r = adjoint_throughput(nx, st, steps=20, warmup=3, d_i=w["d_i"], tau=w["tau_nu"], fields=(u_d, B_d),
+                                   device=dev)
+            adjoint[st] = {"glups": r["glups"], "ms_per_call": r["ms_per_step"], "bytes_per_update": r["bytes_per_update"],
+                           "frac_of_measured_hbm": r["glups"] * r["bytes_per_update"] / peak}
+        torch.cuda.empty_cache()
+
     # Accuracy at the stated step counts (outside the timed region).  The
     # 256^3 recipe is chaotic: differences e-fold every ~20-25 steps, so
     # fields are compared early, spectra by shell.
@@ -562,7 +574,7 @@ def main():
                      "kernel_source_sha256_16": kernel_source_hash()},
         "stated_l2_error": accuracy.get(head, {}).get("vs_oracle_64"),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
-        "variants": variants, "accuracy": accuracy,
+        "variants": variants, "adjoint_step": adjoint, "accuracy": accuracy,
     }
     print(json.dumps(line), flush=True)
 
