@@ -52,7 +52,8 @@ cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 // 21.6 / 22.6, 448 24.3 / 22.6, 512 27.7 / 23.9, 576-832 16.9-20.6 /
 // 20.9-23.0, 896 21.6 / 21.6, 960 23.2 / 21.7, 1024 24.6 / 22.3.  Where it
 // loses, one or two blocks per SM leave 9-13 warps (shared memory and
-// registers per block grow with the row).
+// registers per block grow with the row).  (64- and 128-site rows have run
+// faster since their refill moved into the collision: 28.0 and 31.2.)
 bool row_kernel_wins(int nx) { return (nx <= 512 && nx != 384) || nx >= 960; }
 
 bool step_row_supported(Grid g, int storage, int variant, const void* pop) {
