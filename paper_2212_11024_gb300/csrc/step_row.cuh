@@ -555,11 +555,9 @@ struct RowIO {
     // Two stages: this stage is refilled next, so its rows must have been
     // read out.  Three: the stage refilled next held the previous tile,
     // whose store is the older of the two groups in flight.
-    if (DEFER) {
-    } else if (STAGES == 2) {
-      bulk_wait_read();
-    } else {
-      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    if constexpr (!DEFER) {
+      if (STAGES == 2) bulk_wait_read();
+      else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
     }
     __syncwarp();
   }
@@ -637,8 +635,10 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kR
       auto curl_b = [&](f2 (&J)[3]) {
         const int y = tile % ny, z = tile / ny;
         const long long r0 = ((long long)z * ny + y) * nx;
-        const long long ryp = ((long long)z * ny + wrap(y + 1, ny)) * nx, rym = ((long long)z * ny + wrap(y - 1, ny)) * nx;
-        const long long rzp = ((long long)wrap(z + 1, nz) * ny + y) * nx, rzm = ((long long)wrap(z - 1, nz) * ny + y) * nx;
+        const long long ryp = ((long long)z * ny + wrap(y + 1, ny)) * nx;
+        const long long rym = ((long long)z * ny + wrap(y - 1, ny)) * nx;
+        const long long rzp = ((long long)wrap(z + 1, nz) * ny + y) * nx;
+        const long long rzm = ((long long)wrap(z - 1, nz) * ny + y) * nx;
         const float *Bx = Bfd, *By = Bfd + g.n3, *Bz = Bfd + 2 * g.n3;
         auto at = [&](const float* b, long long r) { return f2{__ldg(reinterpret_cast<const float2*>(b + r + A.x0))}; };
         const f2 by0 = at(By, r0), bz0 = at(Bz, r0);
@@ -675,11 +675,13 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kR
     }
     if (warp == 0) {
       io.template store<kRowStages, kMidRefill>(tile, st);
-      if (kMidRefill) {
-      } else if (kRowStages == 2) {
+      if constexpr (kMidRefill) {
+        // refilled from inside the next tile's collision
+      } else if constexpr (kRowStages == 2) {
         if (tile + 2 * stride < ntiles) io.issue(tile + 2 * stride, st);
       } else {
-        if (tile + (kRowStages - 1) * stride < ntiles) io.issue(tile + (kRowStages - 1) * stride, (it + kRowStages - 1) % kRowStages);
+        const int next = tile + (kRowStages - 1) * stride;
+        if (next < ntiles) io.issue(next, (it + kRowStages - 1) % kRowStages);
       }
     }
   }
