@@ -31,13 +31,24 @@
 namespace flame {
 namespace {
 
-// 128-thread blocks, four per SM (16 warps, 128 registers): the step adjoint
-// keeps much of a site's transposed Jacobian live and waits on its loads, so
-// warps pay more than the ~20 bytes of spills the bound costs (timed against
-// three blocks of 168 registers without spills: 6-13 % faster; against one
-// 256-thread block of 185 registers: 1.5x).
+// 128-thread blocks.  The step adjoint keeps much of a site's transposed
+// Jacobian live and waits on its loads.  With 16-bit storage four blocks per
+// SM (16 warps, 128 registers, ~20 bytes of spills) beat three of 168
+// registers by 13 %; with FP32 storage three blocks that issue the lambda
+// gather together with the state loads (before the forward recompute, so the
+// two latencies overlap; 168 registers, no spills) beat four blocks with the
+// gather after the recompute by 6 % (and one 256-thread block of 185
+// registers by 1.6x).  Issuing the gather early with four blocks, or with
+// 16-bit storage, was slower.
 constexpr int kAdjThreads = 128;
-constexpr int kAdjMinBlocks = 4;
+template <class T>
+__host__ __device__ constexpr bool adj_early_gather() {
+  return sizeof(T) == 4;
+}
+template <class T>
+__host__ __device__ constexpr int adj_min_blocks() {
+  return adj_early_gather<T>() ? 3 : 4;
+}
 
 // 1-D functions of the undivided equilibrium and inverse-moment maps, and
 // their derivatives in u, at velocity component c (index p = c + 1).
@@ -122,7 +133,7 @@ __device__ __forceinline__ void block_sum_to(double v, double* out) {
 }
 
 template <class T, bool ODD>
-__global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
+__global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
     adjoint_step_kernel(Slots<T> P, Grid g, StepConsts k, const float* __restrict__ lam_in,
                         float* __restrict__ lam_out, double* __restrict__ partials) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,6 +145,20 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
     const int site = (z * g.ny + y) * g.nx + x;
     const Nbr nb = make_nbr(x, y, z, g);
     const long long n3 = g.n3;
+
+    // ---- gather dL/df* (streaming transpose: from x + c_q), before or after
+    // the forward recompute (adj_early_gather)
+    float lf[kQ], lg[3][kM];
+    auto gather = [&]() {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) lf[i] = lam_in[(long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int i = 0; i < kM; ++i)
+          lg[b][i] = lam_in[(long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))];
+    };
+    if constexpr (adj_early_gather<T>()) gather();
 
     // ---- forward recompute (deviation variables, as in the step kernel)
     float sf[kQ];
@@ -230,15 +255,7 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
         for (int b = a; b < 3; ++b) D[a][b] = r * (a == b ? S[a][b] - tr3 : S[a][b]);
     }
 
-    // ---- gather dL/df* (streaming transpose: from x + c_q)
-    float lf[kQ], lg[3][kM];
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) lf[i] = lam_in[(long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int i = 0; i < kM; ++i)
-        lg[b][i] = lam_in[(long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))];
+    if constexpr (!adj_early_gather<T>()) gather();
 
     // ---- magnetic collision
     const float omB = k.omegaB;
