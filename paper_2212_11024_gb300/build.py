@@ -36,7 +36,21 @@ def _stale(target, deps):
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    """Compile what is stale and link libflame.so; returns its path.  Callers
+    in several processes (one per GPU rank) are serialised by a file lock, so
+    the first one builds and the others find the objects up to date."""
+    import fcntl
+
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, ptxas_info)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force, verbose, ptxas_info):
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "flame.h")]
     jobs = []
