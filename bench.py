@@ -92,7 +92,7 @@ def parse_variant(spec):
 
 def kernel_name(storage, kernel, n):
     """The step kernel flame_step launches for this storage at n^3."""
-    if kernel == "auto" and storage in ("fp16", "bf16") and n % 64 == 0 and (64 <= n <= 512 and n != 384 or 960 <= n <= 1024):
+    if kernel == "auto" and storage in ("fp16", "bf16") and n % 64 == 0 and 64 <= n <= 1024 and n not in (576, 640):
         return f"step_row_kernel<{storage}> (TMA-staged x rows, packed FP32 pairs)"
     return f"step_kernel<{storage}> (one site per thread)"
 

@@ -97,7 +97,7 @@ typedef struct {
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
     int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant), nx a
-                         multiple of 64 in 64..512 except 384 or in 960..1024 (the row
+                         multiple of 64 in 64..1024 other than 576 and 640 (the row
                          lengths where it was timed faster) and a 16-byte aligned state
                          use the row kernel (x rows staged in shared memory by TMA, two
                          sites per thread in packed FP32 pairs), everything else the

@@ -37,7 +37,7 @@ cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConst
 // The step for 16-bit storage as a persistent kernel over x rows staged in
 // shared memory by TMA, two sites per thread in packed FP32 pairs
 // (step_row.cuh): every variant, 64 <= nx <= 1024 with nx a multiple of 64
-// where the row kernel is the faster one (64-512 except 384, 960-1024), a
+// where the row kernel is the faster one (all but 576 and 640), a
 // 16-byte aligned state.  flag bit 1: a non-finite moment; bit 2: a staged
 // copy did not complete within the wait limit.
 bool step_row_supported(Grid g, int storage, int variant, const void* pop);

@@ -47,14 +47,14 @@ cudaError_t row_maps(const void* pop, const Grid& g, RowMaps* out) {
 cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 
 // Row lengths where the row kernel beats the one-site kernel.  Timed with
-// FP16 storage on 4M-site lattices (GLUPS, row / one-site): 64 26.6 / 23.8,
-// 128 29.8 / 23.9, 192 29.0 / 23.3, 256 30.7 / 23.9, 320 25.2 / 21.1, 384
-// 21.6 / 22.6, 448 24.3 / 22.6, 512 27.7 / 23.9, 576-832 16.9-20.6 /
-// 20.9-23.0, 896 21.6 / 21.6, 960 23.2 / 21.7, 1024 24.6 / 22.3.  Where it
-// loses, one or two blocks per SM leave 9-13 warps (shared memory and
-// registers per block grow with the row).  (64- and 128-site rows have run
-// faster since their refill moved into the collision: 28.0 and 31.2.)
-bool row_kernel_wins(int nx) { return (nx <= 512 && nx != 384) || nx >= 960; }
+// FP16 storage on ~4M-site lattices (nx x m x m, GLUPS, row / one-site): 64
+// 28.0 / 24.1, 128 31.8 / 24.2, 192 29.4 / 23.5, 256 31.2 / 24.2, 320 27.7 /
+// 21.4, 384 26.5 / 23.0, 448 27.9 / 22.9, 512 29.6 / 24.2, 576 20.9 / 22.1,
+// 640 23.0 / 23.2, 704 25.1 / 23.3, 768 26.7 / 24.1, 832 24.6 / 22.6, 896
+// 26.4 / 23.3, 960 27.9 / 23.4, 1024 29.2 / 24.2.  At 576 and 640 sites one
+// block of 288 / 320 threads per SM (96 KB or more of stages) leaves too few
+// warps.
+bool row_kernel_wins(int nx) { return nx != 576 && nx != 640; }
 
 bool step_row_supported(Grid g, int storage, int variant, const void* pop) {
   return variant >= kVarFlame && variant <= kVarFdCurrent && (storage == 2 || storage == 3) && g.nx >= 64 &&

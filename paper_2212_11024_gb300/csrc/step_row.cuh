@@ -20,6 +20,8 @@
 //  - The collision writes its results in place into the staged rows (under
 //    the AA pattern each result lands where the same thread read), and warp
 //    0 writes the tile back with TMA stores to the rows it was loaded from.
+//    Rows longer than 256 sites write their results straight to HBM instead
+//    (their two stages are then refilled without waiting for a store).
 //  - The packed arithmetic halves the FP32 instruction count per site,
 //    which is what limited the one-site kernel with 16-bit storage.
 // The scheme variants are instantiations of the same kernel (template
@@ -492,6 +494,34 @@ struct PairAccess {
   }
 };
 
+// Results of a pair written straight to HBM (rows longer than 256 sites):
+// storage slot s was staged from the row (y, z) + (run_dy(s / 3),
+// run_dz(s / 3)) on odd steps and from (y, z) on even steps, and a result
+// goes to the position of that row it was read from (as st() above does in
+// the staged copy).  yo / zo: the row offsets of y - 1, y, y + 1 and of the
+// planes z - 1, z, z + 1 (periodic).
+template <class T, bool ODD>
+struct PairGlobal {
+  T* state;
+  long long n3;
+  int x0, x1, xm0, xp1;
+  int yo[3], zo[3];
+  __device__ __forceinline__ void st(int s, int d, f2 v) const {
+    const int r = s / 3;
+    const int dy = ODD ? run_dy(r) : 0, dz = ODD ? run_dz(r) : 0;
+    T* row = state + (long long)s * n3 + (zo[dz + 1] + yo[dy + 1]);
+    if (!ODD || d == 0) {
+      Codec2<T>::enc(row + x0, v);
+    } else if (d < 0) {
+      row[xm0] = Codec<T>::enc(v.v.x);
+      row[x0] = Codec<T>::enc(v.v.y);
+    } else {
+      row[x1] = Codec<T>::enc(v.v.x);
+      row[xp1] = Codec<T>::enc(v.v.y);
+    }
+  }
+};
+
 // Warp 0 moves the 48 rows of tile (y, z) between HBM and stage st: the rows
 // (y, z) of all storage slots on even steps, run r of three storage slots
 // from the row (y, z) + (run_dy(r), run_dz(r)) on odd steps.  The store
@@ -604,6 +634,14 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kR
   // of a tile (128^3: 29.9 -> 31.2 GLUPS; at 512-site rows, where a stage is
   // 48 KB and the refill needs its lead time, it was slower: 29.4 -> 28.4).
   constexpr bool kMidRefill = kRowStages == 2 && NX != 0 && NX <= 128;
+  // Rows longer than 256 sites (two stages of up to 96 KB): the results go
+  // straight from registers to HBM and the staged rows are only read, so a
+  // stage is refilled as soon as its tile's collision ends, with no store to
+  // drain first (512^3: 29.4 -> 30.2 GLUPS; 960- and 1024-site rows +7 % /
+  // +4 %; at 256-site rows the extra address arithmetic made it slower).  No
+  // location is read or written by more than one tile, so the order of these
+  // stores and of other tiles' loads does not matter.
+  constexpr bool kDirect = kRowStages == 2 && (NX == 512 || NX == 0);
   if (warp == 0)
     for (int s = 0; s < kAhead; ++s)
       if (first + s * stride < ntiles) io.issue(first + s * stride, s);
@@ -625,11 +663,30 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kR
         return A.ld(ODD ? 26 - q : q, 1 - px);
       };
       auto ldg = [&](int c, int i) { return A.ld(kQ + 3 * (ODD ? opp7(i) : i) + c, -mx7(i)); };
+      PairGlobal<T, ODD> G;
+      if constexpr (kDirect) {
+        const int y = tile % ny, z = tile / ny;
+        G.state = state;
+        G.n3 = g.n3;
+        G.x0 = A.x0;
+        G.x1 = A.x1;
+        G.xm0 = A.xm0;
+        G.xp1 = A.xp1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          G.yo[k] = wrap(y + k - 1, ny) * nx;
+          G.zo[k] = wrap(z + k - 1, nz) * ny * nx;
+        }
+      }
       auto stf = [&](int px, int py, int pz, f2 v) {
         const int q = px + 3 * py + 9 * pz;
-        A.st(ODD ? q : 26 - q, px - 1, v);
+        if constexpr (kDirect) G.st(ODD ? q : 26 - q, px - 1, v);
+        else A.st(ODD ? q : 26 - q, px - 1, v);
       };
-      auto stg = [&](int c, int i, f2 v) { A.st(kQ + 3 * (ODD ? i : opp7(i)) + c, mx7(i), v); };
+      auto stg = [&](int c, int i, f2 v) {
+        if constexpr (kDirect) G.st(kQ + 3 * (ODD ? i : opp7(i)) + c, mx7(i), v);
+        else A.st(kQ + 3 * (ODD ? i : opp7(i)) + c, mx7(i), v);
+      };
       // J = periodic central-difference curl of the pre-collision field at
       // the pair (the face neighbours in y and z are whole-pair loads).
       auto curl_b = [&](f2 (&J)[3]) {
@@ -673,7 +730,10 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kR
           (void)mbar_wait(smem_addr(&bars[j % kRowStages]), (j / kRowStages) & 1, wt.tries);
       return;
     }
-    if (warp == 0) {
+    if (warp == 0 && kDirect) {
+      // the stage was only read: refill it with the tile two ahead
+      if (tile + 2 * stride < ntiles) io.issue(tile + 2 * stride, st);
+    } else if (warp == 0) {
       io.template store<kRowStages, kMidRefill>(tile, st);
       if constexpr (kMidRefill) {
         // refilled from inside the next tile's collision
