@@ -85,6 +85,37 @@ def test_row_kernel_graph_replay_is_bit_identical():
     b.close()
 
 
+# one lattice per pipeline kind: 64 (two stages, refill inside the
+# collision), 256 (three stages, in-place TMA stores), 512 and 960 (two
+# stages, direct stores; compile-time and general row length)
+@pytest.mark.parametrize("shape,storage", [((4, 3, 64), "fp16"), ((2, 3, 256), "bf16"), ((2, 3, 512), "fp16"),
+                                           ((2, 1, 960), "bf16")])
+def test_wait_limit_on_every_pipeline(shape, storage):
+    """A stalled step (barriers armed, copies never issued, 256 polls) on
+    each pipeline of the row kernel reports FLAME_ERR_TIMEOUT, leaves the
+    state and step count as they were, and the next step is normal."""
+    import torch
+    from paper_2212_11024_gb300 import Flame, FlameError
+    from paper_2212_11024_gb300.flame import FLAME_ERR_TIMEOUT
+    nz, ny, nx = shape
+    u, B = _fields(shape, 49)
+    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0))
+    ref = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0))
+    for s in (sim, ref):
+        s.init(None, u, B)
+        s.step(2)
+    sim.debug_stall_next_step(256)
+    with pytest.raises(FlameError) as e:
+        sim.step(1)
+    assert e.value.status == FLAME_ERR_TIMEOUT
+    assert sim.info()["step"] == 2
+    assert torch.equal(sim.get_state()[0], ref.get_state()[0])
+    sim.close()
+    ref.step(1)
+    assert ref.sync() is None
+    ref.close()
+
+
 def test_row_kernel_wait_limit_reports_timeout():
     """The row kernel's bounded waits: a step whose barriers are armed but
     never fed gives FLAME_ERR_TIMEOUT after the poll limit, leaves the state
