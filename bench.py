@@ -171,16 +171,24 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle timing
+def host_cores():
+    """The host cores this process may run on (a launcher such as torchrun
+    sets OMP_NUM_THREADS=1 per rank; the oracle legs run on rank 0 alone and
+    use all of them)."""
+    return len(os.sched_getaffinity(0))
+
+
 def oracle_mlups(n, steps, threads=0):
     """Time `steps` oracle steps (literal 27x27 mode, FP64, OpenMP) on an n^3
-    instance of the workload recipe; returns (MLUPS, seconds, cores)."""
+    instance of the workload recipe; returns (MLUPS, seconds, cores).
+    threads = 0: all host cores."""
     import numpy as np
 
     import oracle as O
     from paper_2212_11024_gb300 import inputs
 
     w = workload(n)
-    cores = O.threads(threads)
+    cores = O.threads(threads if threads > 0 else host_cores())
     u, B = inputs.turbulence((n, n, n), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
     p = O.Params(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"])
     pop = O.init(p, None, u, B)
@@ -208,7 +216,7 @@ def run_reference(args):
     from paper_2212_11024_gb300 import inputs
 
     w = workload(n)
-    cores = O.threads(0)
+    cores = O.threads(host_cores())
     u, B = inputs.turbulence((n, n, n), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
     p = O.Params(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"])
     pop = O.init(p, None, u, B)
