@@ -283,6 +283,7 @@ def oracle_restriction_errors(storages, dev):
     w = workload(n)
     u, B = inputs.turbulence((n, n, n), w["seed_u"], w["seed_b"], w["rms"], w["rms"], shells=w["shells"])
     O.build()
+    O.threads(host_cores())
     p = O.Params(n, n, n, w["tau_nu"], w["tau_eta"], w["d_i"])
     pop = O.init(p, None, u, B)
     O.step(p, pop, steps, literal=True)
