@@ -594,17 +594,13 @@ struct RowIO {
 };
 
 // Launch bounds per instantiation: 128 registers per thread (512 threads'
-// worth per SM), except a 256-site row (128 threads) with three stages,
-// which fits three blocks per SM by shared memory and so may use up to 168
-// registers per thread at no cost in occupancy.
+// worth per SM).
 constexpr int row_bound_threads(int nx) { return nx ? nx / 2 : kRowMaxThreads; }
-constexpr int row_bound_blocks(int nx, int stages) {
-  return nx == 256 && stages == 3 ? 3 : 512 / row_bound_threads(nx);
-}
+constexpr int row_bound_blocks(int nx) { return 512 / row_bound_threads(nx); }
 
 // Bfd: the pre-collision B - B_ref ([3][N3] floats), read by kVarFdCurrent only.
 template <class T, bool ODD, int NX, int kRowStages, int VAR>
-__global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kRowStages))
+__global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
     step_row_kernel(T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
                     const float* __restrict__ Bfd, const __grid_constant__ RowMaps maps, RowWait wt) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -628,12 +624,14 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX, kR
   // Tiles staged before the loop: both stages with two; with three, two of
   // them (the third is filled once the first tile's store has drained).
   constexpr int kAhead = kRowStages == 2 ? 2 : kRowStages - 1;
-  // Short rows with two stages (64 and 128 sites: many small blocks per SM)
-  // refill the stage of the previous tile from inside the collision of the
-  // next one, so warp 0 no longer waits for that store to drain at the end
-  // of a tile (128^3: 29.9 -> 31.2 GLUPS; at 512-site rows, where a stage is
-  // 48 KB and the refill needs its lead time, it was slower: 29.4 -> 28.4).
-  constexpr bool kMidRefill = kRowStages == 2 && NX != 0 && NX <= 128;
+  // Rows of up to 256 sites with two stages (stages of up to 24.6 KB, four
+  // or more blocks per SM) refill the stage of the previous tile from inside
+  // the collision of the next one, so warp 0 no longer waits for that store
+  // to drain at the end of a tile (128^3: 29.9 -> 31.2 GLUPS; 256^3, where
+  // it also beats three stages of three blocks: 32.15 -> 32.9; at 512-site
+  // rows, where a stage is 48 KB and the refill needs its lead time, it was
+  // slower: 29.4 -> 28.4).
+  constexpr bool kMidRefill = kRowStages == 2 && NX != 0 && NX <= 256;
   // Rows longer than 256 sites (two stages of up to 96 KB): the results go
   // straight from registers to HBM and the staged rows are only read, so a
   // stage is refilled as soon as its tile's collision ends, with no store to
@@ -752,13 +750,15 @@ size_t row_smem_bytes(int nx, size_t elem, int stages) {
   return stages * (kPop * (size_t)nx * elem + sizeof(unsigned long long));
 }
 
-// Stages per row length, from timings of both at 128^3, 256^3 and 512^3
-// (FP16): three stages (the store of a tile drains while the next one is
-// computed) win for rows of 129..256 sites (31.6 against 30.7 GLUPS at
-// 256^3); two win for shorter rows, where more blocks fit per SM (28.6
-// against 28.2 at 128^3), and for 512-site rows, where three stages leave
-// one block per SM (30.1 against 17.5 at 512^3).
-constexpr int row_stages(int nx) { return nx > 128 && nx <= 256 ? 3 : 2; }
+// Stages per row length, from timings at 128^3, 256^3 and 512^3 (FP16).
+// Two stages, with the refill issued inside the next tile's collision (up
+// to 256 sites) or with direct stores (longer rows): four blocks per SM at
+// 256-site rows (32.9 GLUPS against 32.15 for three stages of three
+// blocks, where the store of a tile drains while the next one computes),
+// and one block instead of two at 512-site rows with three (17.5 against
+// 30.1).  The general instantiation keeps three stages between 129 and 255
+// sites (192: the refill inside the collision was not timed there).
+constexpr int row_stages(int nx) { return nx > 128 && nx < 256 ? 3 : 2; }
 
 // Launch configuration of one instantiation, cached per device (the
 // shared-memory opt-in and the resident blocks per SM depend on the device
