@@ -7,9 +7,23 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "flame.h"
 #include "flame_internal.h"
 #include "lattice.cuh"
+
+namespace {
+// An NVTX range over one entry point: the host-side span of each call shows on
+// a profiler's timeline (header-only NVTX; without a tool attached a push and
+// a pop cost a few nanoseconds).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+}  // namespace
 
 struct flame_ctx {
   flame_params p;
@@ -214,6 +228,7 @@ flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state,
 
 flame_status flame_init(flame_ctx* c, const double* d_rho, const double* d_u, const double* d_B,
                         const double* d_gradu, const double* d_gradB) {
+  const Range range("flame_init");
   if (!c) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
   if (!d_u || !d_B) return FLAME_ERR_PARAM;
@@ -271,6 +286,7 @@ static cudaError_t capture_graph(flame_ctx* c, int parity) {
 }
 
 flame_status flame_step(flame_ctx* c, int n) {
+  const Range range("flame_step");
   flame_status st = usable(c);
   if (st != FLAME_OK) return st;
   if (n < 0) return FLAME_ERR_PARAM;
@@ -331,6 +347,7 @@ flame_status flame_info(flame_ctx* c, flame_info_t* out) {
 }
 
 flame_status flame_moments(flame_ctx* c, double* d_rho, double* d_u, double* d_B, double* d_J) {
+  const Range range("flame_moments");
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
@@ -339,6 +356,7 @@ flame_status flame_moments(flame_ctx* c, double* d_rho, double* d_u, double* d_B
 }
 
 flame_status flame_populations(flame_ctx* c, double* d_f) {
+  const Range range("flame_populations");
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
@@ -347,6 +365,7 @@ flame_status flame_populations(flame_ctx* c, double* d_f) {
 }
 
 flame_status flame_probe(flame_ctx* c, int nsites, const long long* d_sites, double* d_out) {
+  const Range range("flame_probe");
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
@@ -356,6 +375,7 @@ flame_status flame_probe(flame_ctx* c, int nsites, const long long* d_sites, dou
 }
 
 flame_status flame_reduce(flame_ctx* c, double* h) {
+  const Range range("flame_reduce");
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
@@ -401,6 +421,7 @@ flame_status flame_reduce(flame_ctx* c, double* h) {
 }
 
 flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb) {
+  const Range range("flame_spectra");
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
@@ -494,6 +515,7 @@ flame_status flame_set_state(flame_ctx* c, const void* d_src, long long step, in
 
 flame_status flame_step_adjoint(flame_ctx* c, const void* d_state, int parity, const float* d_adj_in,
                                 float* d_adj_out, double* d_ddi) {
+  const Range range("flame_step_adjoint");
   if (!c || !d_state || !d_adj_in || !d_adj_out || !d_ddi) return FLAME_ERR_PARAM;
   if (c->p.variant != FLAME_SCHEME) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
@@ -513,6 +535,7 @@ flame_status flame_step_adjoint(flame_ctx* c, const void* d_state, int parity, c
 
 flame_status flame_init_adjoint(flame_ctx* c, const double* d_u, const double* d_B, const float* d_adj0,
                                 double* d_ubar, double* d_Bbar, double* d_ddi) {
+  const Range range("flame_init_adjoint");
   if (!c || !d_u || !d_B || !d_adj0 || !d_ddi || (!d_ubar && !d_Bbar)) return FLAME_ERR_PARAM;
   if (c->p.variant != FLAME_SCHEME) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
