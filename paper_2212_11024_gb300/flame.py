@@ -136,6 +136,31 @@ def state_bytes(p: Params) -> int:
     return int(_lib().flame_state_bytes(ctypes.byref(p)))
 
 
+# Checkpoints (save_checkpoint / load_checkpoint): the state blob with its
+# step and AA parity, and the parameters it depends on.  The lattice, the
+# storage type and the reference state of the deviation encoding (rho0,
+# B_ref) define what the bytes mean and must match to resume; the relaxation
+# times, d_i and the variant define the dynamics and must match too unless
+# the caller asks to resume with new ones.
+CHECKPOINT_LAYOUT = ("nx", "ny", "nz", "storage", "rho0", "B_ref")
+CHECKPOINT_PHYSICS = ("tau_nu", "tau_eta", "d_i", "variant")
+
+
+def checkpoint_meta(p: Params) -> dict:
+    """The parameters a checkpoint records (plain Python values)."""
+    meta = {k: getattr(p, k) for k in CHECKPOINT_LAYOUT + CHECKPOINT_PHYSICS if k != "B_ref"}
+    meta["B_ref"] = [float(v) for v in p.B_ref]
+    return meta
+
+
+def checkpoint_mismatches(saved: dict, p: Params, same_physics: bool = True) -> list:
+    """Names of the recorded parameters that differ from p (the layout ones
+    always, the physics ones when same_physics)."""
+    cur = checkpoint_meta(p)
+    keys = CHECKPOINT_LAYOUT + (CHECKPOINT_PHYSICS if same_physics else ())
+    return [k for k in keys if not np.array_equal(np.asarray(saved[k]), np.asarray(cur[k]))]
+
+
 def _check(rc, what):
     if rc != FLAME_OK:
         raise FlameError(rc, what)
@@ -288,8 +313,34 @@ class Flame:
     def set_state(self, src, step, parity):
         if src.numel() != self.state.numel() or src.dtype != self.state.dtype:
             raise ValueError("state blob does not match these parameters")
-        _check(self._lib.flame_set_state(self._ctx_or_raise(), self._ptr(src.contiguous()), int(step), int(parity)),
+        src = src.contiguous()
+        # the copy runs on the library's stream: keep src's memory from being
+        # reused by the caching allocator until it is done
+        src.record_stream(self.stream)
+        _check(self._lib.flame_set_state(self._ctx_or_raise(), self._ptr(src), int(step), int(parity)),
                "flame_set_state")
+
+    def save_checkpoint(self, path):
+        """Write the state, its step and parity and checkpoint_meta() to an
+        .npz file (the state goes through host memory)."""
+        blob, step, parity = self.get_state()
+        meta = checkpoint_meta(self.p)
+        np.savez(path, state=blob.cpu().numpy(), step=np.int64(step), parity=np.int32(parity),
+                 **{"meta_" + k: np.asarray(v) for k, v in meta.items()})
+
+    def load_checkpoint(self, path, same_physics=True):
+        """Resume from a save_checkpoint file.  Raises ValueError when the
+        recorded lattice, storage or reference state differ from this run's
+        (and its relaxation times, d_i or variant, unless same_physics is
+        False)."""
+        with np.load(path) as z:
+            saved = {k[5:]: z[k] for k in z.files if k.startswith("meta_")}
+            bad = checkpoint_mismatches(saved, self.p, same_physics)
+            if bad:
+                raise ValueError(f"checkpoint {path} does not match this run: {', '.join(bad)}")
+            blob = self.torch.from_numpy(z["state"]).to(self.device)
+            step, parity = int(z["step"]), int(z["parity"])
+        self.set_state(blob, step, parity)
 
     def close(self):
         if getattr(self, "_ctx", None) is not None:
