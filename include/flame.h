@@ -276,7 +276,7 @@ flame_status flame_reduce_static(flame_ctx *ctx, int nblocks, double *d_scalars)
  * `tries` polls per wait, synchronises, and returns FLAME_ERR_TIMEOUT
  * (sticky, like any failure); the state and the step count are left as they
  * were.  Errors: FLAME_ERR_PARAM (tries == 0, or the context does not run
- * the row kernel: FP16/BF16 storage, FLAME_SCHEME, kernel = 0, nx as listed
+ * the row kernel: FP16/BF16 storage (any variant), kernel = 0, nx as listed
  * at flame_params.kernel), FLAME_ERR_STATE (before flame_init). */
 flame_status flame_debug_stall_next_step(flame_ctx *ctx, unsigned tries);
 
