@@ -90,7 +90,7 @@ def test_row_kernel_graph_replay_is_bit_identical():
 # stages, direct stores; compile-time and general row length)
 @pytest.mark.parametrize("shape,storage", [((4, 3, 64), "fp16"), ((2, 3, 256), "bf16"), ((2, 3, 512), "fp16"),
                                            ((2, 1, 960), "bf16")])
-def test_wait_limit_on_every_pipeline(shape, storage):
+def test_wait_limit_on_every_pipeline(shape, storage, variant="flame"):
     """A stalled step (barriers armed, copies never issued, 256 polls) on
     each pipeline of the row kernel reports FLAME_ERR_TIMEOUT, leaves the
     state and step count as they were, and the next step is normal."""
@@ -99,8 +99,8 @@ def test_wait_limit_on_every_pipeline(shape, storage):
     from paper_2212_11024_gb300.flame import FLAME_ERR_TIMEOUT
     nz, ny, nx = shape
     u, B = _fields(shape, 49)
-    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0))
-    ref = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0))
+    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), variant=variant)
+    ref = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), variant=variant)
     for s in (sim, ref):
         s.init(None, u, B)
         s.step(2)
@@ -114,6 +114,13 @@ def test_wait_limit_on_every_pipeline(shape, storage):
     ref.step(1)
     assert ref.sync() is None
     ref.close()
+
+
+@pytest.mark.parametrize("variant,shape", [("bgk", (2, 3, 256)), ("fd_current", (2, 3, 512)), ("emhd", (4, 3, 64))])
+def test_wait_limit_for_the_variants(variant, shape):
+    """The same for the scheme variants (the finite-difference current's
+    stalled step reads no B field: its waits end before the collision)."""
+    test_wait_limit_on_every_pipeline(shape, "fp16", variant)
 
 
 def test_row_kernel_wait_limit_reports_timeout():
