@@ -192,12 +192,12 @@ flame_status flame_probe(flame_ctx *ctx, int nsites, const long long *d_sites, d
  * Asynchronous. */
 flame_status flame_populations(flame_ctx *ctx, double *d_f);
 
-/* FP64 scalar diagnostics of the current state (Sec. 4.3, 5: energies,
+/* FP64 scalar diagnostics of the current state (Sec. 4.4, 5: energies,
  * cross-helicity, magnetic dissipation, div B estimate).  h_scalars has
  * FLAME_NSCALARS entries (indices FLAME_S_*).  Synchronises. */
 flame_status flame_reduce(flame_ctx *ctx, double *h_scalars);
 
-/* Shell energy spectra of u and B - <B> (Sec. 4.3): with
+/* Shell energy spectra of u and B - <B> (Sec. 4.4): with
  * F_hat(m) = N3^-1 sum_x F(x) exp(-2 pi i m.x/N), h_Eu[n] and h_Eb[n] are
  * 1/2 sum |F_hat|^2 over the modes with round(|m|) = n, n = 0..nshell-1
  * (modes beyond are dropped; summed over every shell they give 1/2<|F|^2>);

@@ -16,6 +16,9 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   streaming, initialisation: pinned (moment identities, closed forms,
   brute-force literal-vs-factored, BGK limit, exact damped wave, order of
   convergence, conservation).
+- shell spectra, scalar diagnostics, energy budget (``spectra``): pinned
+  (single-mode shells, Parseval, closed-form scalars, single-mode budget,
+  the budget identity on a stepped run).
 - turbulence beyond early times: parity unpinned (chaotic; compared per
   field only at early times and per spectral shell).
 """

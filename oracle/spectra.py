@@ -1,6 +1,12 @@
-"""Shell energy spectra and scalar diagnostics, FP64 numpy (Sec. 4.3, 5).
+"""Shell energy spectra and scalar diagnostics, FP64 numpy (Sec. 4.4, 5).
 
 TEST INFRASTRUCTURE (see ``oracle/__init__.py``).
+
+Pinned in ``tests/test_oracle_spectra_pins.py``: single Fourier modes land
+in the one shell round(|m|) with their closed-form energy (cubic, non-cubic,
+odd grids, Nyquist modes), Parseval, closed-form scalars of shear modes, the
+budget of a single mode (S = 0, D = 2 nu k^2 E), and the budget identity
+d/dt sum_{n'<n} E = -S(n) - D(n) on a stepped oracle run.
 
 Conventions (the paper normalises spectra by the total energy but does not
 fix the binning):
@@ -72,7 +78,7 @@ def scalars(rho, u, B, J):
 
 
 def energy_budget(u, B, nu, eta, nshell, d_i=0.0):
-    """(E, S, D) of Sec. 4.3 (eq. mhd_en_trans), numpy FP64, written mode by
+    """(E, S, D) of Sec. 4.4 (eq. mhd_en_trans), numpy FP64, written mode by
     mode from the definitions: F = FFT/N3, k = 2 pi m/N (Nyquist k = 0 for
     derivatives), J = curl B spectrally, V = u - d_i J; S(n), D(n) sum the
     modes with round|m| < n; E(n) = 1/2 sum_{shell n} |F(u)|^2 + |F(B)|^2."""

@@ -16,7 +16,7 @@ current obtained from the magnetic non-equilibrium moments.
                 (FlameBandEnergy autograd Function, sqrt(N) checkpointing).
 - ``turbulence``: decaying-turbulence runs with spectra and step throughput.
 - ``throughput``: step throughput of any variant, storage and kernel.
-- ``budget``  : the wavenumber energy budget S(k), D(k) of Sec. 4.3 (torch.fft).
+- ``budget``  : the wavenumber energy budget S(k), D(k) of Sec. 4.4 (torch.fft).
 - ``validation``: the Table 1 three-mode runs and the paper's error metrics.
 - ``build``   : nvcc build of libflame.so for sm_103a.
 """

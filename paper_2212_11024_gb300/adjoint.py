@@ -2,7 +2,7 @@
 
 The loss is the magnetic energy in a band of spectral shells at the last
 step, L = sum_{lo <= n <= hi} E_B(n) with E_B(n) = 1/2 sum_{round|m| = n}
-|B_hat(m)|^2 and B_hat = FFT(B) / N3 (the spectra of Sec. 4.3).  Its
+|B_hat(m)|^2 and B_hat = FFT(B) / N3 (the spectra of Sec. 4.4).  Its
 gradient with respect to the initial magnetic field, the initial velocity
 and the Hall length d_i comes from the library's hand-written adjoints
 (flame_step_adjoint, flame_init_adjoint), run backwards over the stored

@@ -1,4 +1,4 @@
-"""Wavenumber energy budget of Sec. 4.3 (eq. mhd_en_trans), on the GPU.
+"""Wavenumber energy budget of Sec. 4.4 (eq. mhd_en_trans), on the GPU.
 
 For fields u, B on the periodic lattice (lattice units, F(f) = FFT(f)/N3,
 k = 2 pi m / N per axis, spectral derivatives with the Nyquist wavenumber

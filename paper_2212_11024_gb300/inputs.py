@@ -16,7 +16,7 @@ macroscopic fields the paper starts its runs from.
   second-order central-difference divergence of the sampled field vanishes.
   Mode amplitudes are drawn over the fixed cube |m_a| <= hi in a fixed order,
   so a given seed gives the same modes on every grid size.
-- ``orszag_tang``: the 3-D Orszag-Tang vortex of Sec. 4.3 on a 2 pi box.
+- ``orszag_tang``: the 3-D Orszag-Tang vortex of Sec. 4.4 on a 2 pi box.
 """
 from __future__ import annotations
 
@@ -115,7 +115,7 @@ def turbulence(shape, seed_u, seed_b, rms_u=0.05, rms_b=0.05, shells=(1, 4)):
 
 
 def orszag_tang(shape, u0=1.0, b0=0.8, scale=1.0):
-    """Sec. 4.3 Orszag-Tang vortex on a 2 pi box sampled at N points per side.
+    """Sec. 4.4 Orszag-Tang vortex on a 2 pi box sampled at N points per side.
 
     u = u0 [-2 sin y, 2 sin x, 0], B = b0 [-2 sin 2y + sin z, 2 sin x + sin z,
     sin x + sin y]; both multiplied by ``scale`` (the lattice velocity unit)."""

@@ -1,4 +1,4 @@
-"""Energy budget of Sec. 4.3: the GPU-side torch implementation against the
+"""Energy budget of Sec. 4.4: the GPU-side torch implementation against the
 numpy FP64 oracle implementation (on CPU tensors here), and the properties the
 mathematics fixes: for spectrally solenoidal fields the nonlinear flux through
 a sphere enclosing every mode vanishes (energy conservation of the ideal

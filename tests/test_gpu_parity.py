@@ -320,7 +320,7 @@ def test_scheme_variants_match_oracle(variant):
 
 
 def test_orszag_tang_run_and_energy_budget():
-    """Orszag-Tang vortex (Sec. 4.3) at 32^3 (U0 = 0.05/sqrt(3), B0 = 0.8 U0,
+    """Orszag-Tang vortex (Sec. 4.4) at 32^3 (U0 = 0.05/sqrt(3), B0 = 0.8 U0,
     tau = 0.6), 40 steps through the library; the budget of the resulting
     fields computed on the GPU (budget.energy_budget on CUDA tensors) equals
     the numpy FP64 oracle implementation on the same fields."""
