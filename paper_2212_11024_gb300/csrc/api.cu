@@ -176,6 +176,8 @@ int flame_ctx_view(const flame_ctx* c, flame::CtxView* v) {
   return 0;
 }
 
+int flame_ctx_cuda_fail(flame_ctx* c, cudaError_t e) { return (int)cuda_fail(c, e); }
+
 extern "C" {
 
 size_t flame_state_bytes(const flame_params* p) {

@@ -118,3 +118,7 @@ cudaError_t launch_shell_bin(const void* spec /* cufftDoubleComplex */, Grid g, 
 struct flame_ctx;
 // Fills *v from the context; returns 0, or -1 for a null context.
 int flame_ctx_view(const flame_ctx* c, flame::CtxView* v);
+// Records a failed CUDA call in the context's sticky status, as the entry
+// points of api.cu do (FLAME_ERR_CUDA unless an error is already recorded);
+// returns FLAME_ERR_CUDA, or FLAME_OK for e == cudaSuccess.
+int flame_ctx_cuda_fail(flame_ctx* c, cudaError_t e);

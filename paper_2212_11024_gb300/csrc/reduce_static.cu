@@ -105,11 +105,13 @@ extern "C" flame_status flame_reduce_static(flame_ctx* ctx, int nblocks, double*
     if (want > FLAME_STATIC_REDUCE_BLOCKS_MAX) want = FLAME_STATIC_REDUCE_BLOCKS_MAX;
     nblocks = want < 1 ? 1 : (int)want;
   }
+  // failures are recorded in the context's sticky status, as in flame_reduce
   double* scratch = nullptr;
-  if (scratch_address(v.device, &scratch) != cudaSuccess) return FLAME_ERR_CUDA;
-  cudaError_t e = flame::launch_reduce_partials(v.storage, v.parity, v.state, v.g, v.k, nblocks, scratch, v.stream);
-  if (e != cudaSuccess) return FLAME_ERR_CUDA;
+  cudaError_t e = scratch_address(v.device, &scratch);
+  if (e != cudaSuccess) return static_cast<flame_status>(flame_ctx_cuda_fail(ctx, e));
+  e = flame::launch_reduce_partials(v.storage, v.parity, v.state, v.g, v.k, nblocks, scratch, v.stream);
+  if (e != cudaSuccess) return static_cast<flame_status>(flame_ctx_cuda_fail(ctx, e));
   finalize_kernel<<<1, 32, 0, v.stream>>>(scratch, nblocks, (double)v.g.n3, v.Bref[0], v.Bref[1], v.Bref[2],
                                           d_scalars);
-  return cudaGetLastError() == cudaSuccess ? FLAME_OK : FLAME_ERR_CUDA;
+  return static_cast<flame_status>(flame_ctx_cuda_fail(ctx, cudaGetLastError()));
 }

@@ -218,16 +218,39 @@ class Flame:
             raise RuntimeError("context closed")
         return self._ctx
 
+    # The library queues its work on self.stream, torch on its current
+    # stream; when a caller passes another stream the two are ordered here.
+    def _before(self):
+        """Make the library's stream wait for torch's current stream, so that
+        inputs torch wrote, and outputs torch allocated, are ready before the
+        library touches them.  Returns the current stream."""
+        cur = self.torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+        return cur
+
+    def _after(self, cur, *tensors):
+        """Make torch's current stream wait for the library's, so that torch
+        reads the outputs only once they are written, and keep the tensors'
+        memory from being reused by the caching allocator while the library's
+        stream still uses it."""
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+            for t in tensors:
+                if t is not None:
+                    t.record_stream(self.stream)
+
     # ------------------------------------------------------------------- API
     def init(self, rho, u, B, gradu=None, gradB=None):
         """flame_init from FP64 fields (numpy or torch): rho [nz,ny,nx] or None,
         u, B [3,nz,ny,nx], optional gradients [9,nz,ny,nx]."""
         r, uu, bb = self._dev(rho, 0), self._dev(u, 3), self._dev(B, 3)
         gu, gb = self._dev(gradu, 9), self._dev(gradB, 9)
-        with self.torch.cuda.device(self.device), self.torch.cuda.stream(self.stream):
-            # flame_init synchronises the stream, so the temporaries outlive their use
-            rc = self._lib.flame_init(self._ctx_or_raise(), self._ptr(r), self._ptr(uu), self._ptr(bb),
-                                      self._ptr(gu), self._ptr(gb))
+        cur = self._before()
+        # flame_init synchronises the library's stream, so the temporaries outlive their use
+        rc = self._lib.flame_init(self._ctx_or_raise(), self._ptr(r), self._ptr(uu), self._ptr(bb),
+                                  self._ptr(gu), self._ptr(gb))
+        self._after(cur)
         _check(rc, "flame_init")
 
     def step(self, n=1):
@@ -249,8 +272,11 @@ class Flame:
                        u=t.empty((3,) + self.shape, dtype=t.float64, device=self.device),
                        B=t.empty((3,) + self.shape, dtype=t.float64, device=self.device),
                        J=t.empty((3,) + self.shape, dtype=t.float64, device=self.device))
-        _check(self._lib.flame_moments(self._ctx_or_raise(), self._ptr(out.get("rho")), self._ptr(out.get("u")),
-                                       self._ptr(out.get("B")), self._ptr(out.get("J"))), "flame_moments")
+        cur = self._before()
+        rc = self._lib.flame_moments(self._ctx_or_raise(), self._ptr(out.get("rho")), self._ptr(out.get("u")),
+                                     self._ptr(out.get("B")), self._ptr(out.get("J")))
+        self._after(cur, *out.values())
+        _check(rc, "flame_moments")
         return out
 
     def probe(self, sites, out=None):
@@ -260,14 +286,20 @@ class Flame:
         n = int(sites.numel())
         if out is None:
             out = t.empty((n, 10), dtype=t.float64, device=self.device)
-        _check(self._lib.flame_probe(self._ctx_or_raise(), n, self._ptr(sites), self._ptr(out)), "flame_probe")
+        cur = self._before()
+        rc = self._lib.flame_probe(self._ctx_or_raise(), n, self._ptr(sites), self._ptr(out))
+        self._after(cur, sites, out)
+        _check(rc, "flame_probe")
         return out
 
     def populations(self):
         """Decoded pre-collision populations [48, nz, ny, nx], FP64, natural slot order."""
         t = self.torch
         f = t.empty((48,) + self.shape, dtype=t.float64, device=self.device)
-        _check(self._lib.flame_populations(self._ctx_or_raise(), self._ptr(f)), "flame_populations")
+        cur = self._before()
+        rc = self._lib.flame_populations(self._ctx_or_raise(), self._ptr(f))
+        self._after(cur, f)
+        _check(rc, "flame_populations")
         return f
 
     def reduce(self) -> dict:
@@ -287,8 +319,10 @@ class Flame:
         t = self.torch
         if out is None:
             out = t.empty(NSCALARS, dtype=t.float64, device=self.device)
-        _check(self._lib.flame_reduce_static(self._ctx_or_raise(), int(nblocks), self._ptr(out)),
-               "flame_reduce_static")
+        cur = self._before()
+        rc = self._lib.flame_reduce_static(self._ctx_or_raise(), int(nblocks), self._ptr(out))
+        self._after(cur, out)
+        _check(rc, "flame_reduce_static")
         return out
 
     def spectra(self, nshell):
@@ -306,19 +340,20 @@ class Flame:
         dst = self.torch.empty_like(self.state)
         step = ctypes.c_longlong()
         par = ctypes.c_int()
-        _check(self._lib.flame_get_state(self._ctx_or_raise(), self._ptr(dst), ctypes.byref(step), ctypes.byref(par)),
-               "flame_get_state")
+        cur = self._before()
+        rc = self._lib.flame_get_state(self._ctx_or_raise(), self._ptr(dst), ctypes.byref(step), ctypes.byref(par))
+        self._after(cur, dst)
+        _check(rc, "flame_get_state")
         return dst, int(step.value), int(par.value)
 
     def set_state(self, src, step, parity):
         if src.numel() != self.state.numel() or src.dtype != self.state.dtype:
             raise ValueError("state blob does not match these parameters")
         src = src.contiguous()
-        # the copy runs on the library's stream: keep src's memory from being
-        # reused by the caching allocator until it is done
-        src.record_stream(self.stream)
-        _check(self._lib.flame_set_state(self._ctx_or_raise(), self._ptr(src), int(step), int(parity)),
-               "flame_set_state")
+        cur = self._before()
+        rc = self._lib.flame_set_state(self._ctx_or_raise(), self._ptr(src), int(step), int(parity))
+        self._after(cur, src)
+        _check(rc, "flame_set_state")
 
     def save_checkpoint(self, path):
         """Write the state, its step and parity and checkpoint_meta() to an

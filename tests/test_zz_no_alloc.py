@@ -4,11 +4,13 @@ Some callers cannot let the library call cudaMalloc: cudaMalloc may
 synchronise the device and stall work already queued, and some hosts hand
 every byte of device memory to their own caching allocator.  This entry
 point keeps its scratch in a fixed device array instead.  The test calls it
-through the C ABI twice in a row, with different block counts so that a
-second call reading stale partial sums of the first would show, and checks
-each result against flame_reduce, which computes the same sums with its own
-workspace.  It also checks that block counts beyond the array's capacity are
-rejected.
+through the C ABI twice in a row and checks each result against
+flame_reduce, which computes the same sums with its own workspace.  The
+first call uses few blocks (37) and the second many (600), so the second
+call reads array entries the first never wrote: if a block's partial sums
+were not written before they are read, the second result would pick up the
+array's initial zeros and differ.  It also checks that block counts beyond
+the array's capacity are rejected.
 """
 import ctypes
 
@@ -19,16 +21,29 @@ from gpu_helpers import turbulence
 
 pytestmark = pytest.mark.gpu
 
-# The two entry points run the same FP64 reduction kernel; only the order of
-# the final host/device arithmetic may differ, at the level of FP64 rounding.
+# The two entry points run the same FP64 reduction kernel with different
+# block counts, so the per-site terms are summed in a different order.  Sums
+# of positive terms (mass, energies, <|J|^2>, the div B estimate) then agree
+# to a relative 1e-12.  Sums that cancel (momentum, <B> with a mean field
+# removed, the cross-helicity after the mean-field correction) can end near
+# zero, so they get an absolute bound of 1e-13 times the sum of the terms'
+# magnitudes, estimated from the field scales; the maximum and the
+# non-finite count do not depend on the order.
 RTOL = 1e-12
 
 
-def _compare(static, ref):
+def _compare(static, ref, n3, u_max, b_scale):
     from paper_2212_11024_gb300.flame import SCALAR_NAMES
+    atol = {"mom_x": n3 * u_max, "mom_y": n3 * u_max, "mom_z": n3 * u_max,
+            "B_x": b_scale, "B_y": b_scale, "B_z": b_scale, "H_c": u_max * b_scale}
     for i, name in enumerate(SCALAR_NAMES):
         a, b = float(static[i]), float(ref[name])
-        assert abs(a - b) <= RTOL * max(abs(b), 1e-300) + 1e-300, (name, a, b)
+        if name in ("u_max", "nonfinite"):
+            assert a == b, (name, a, b)
+        elif name in atol:
+            assert abs(a - b) <= 1e-13 * atol[name], (name, a, b)
+        else:
+            assert abs(a - b) <= RTOL * abs(b), (name, a, b)
 
 
 def test_reduce_static_matches_reduce_on_two_calls():
@@ -46,21 +61,26 @@ def test_reduce_static_matches_reduce_on_two_calls():
     lib = library()
     out = torch.full((NSCALARS,), float("nan"), dtype=torch.float64, device=sim.device)
 
-    # first call (first use of the scratch array in this process, odd parity)
-    rc = lib.flame_reduce_static(sim._ctx, 600, ctypes.c_void_p(out.data_ptr()))
-    assert rc == FLAME_OK
-    torch.cuda.synchronize()
-    first = out.cpu().numpy().copy()
-    _compare(first, sim.reduce())
+    n3 = nx * ny * nz
+    b_scale = float(np.abs(B).max())
 
-    # second call on a changed state and with fewer blocks
-    sim.step(4)
-    out.fill_(float("nan"))
+    # first call (odd parity) with few blocks
     rc = lib.flame_reduce_static(sim._ctx, 37, ctypes.c_void_p(out.data_ptr()))
     assert rc == FLAME_OK
     torch.cuda.synchronize()
+    first = out.cpu().numpy().copy()
+    ref = sim.reduce()
+    _compare(first, ref, n3, ref["u_max"], b_scale)
+
+    # second call on a changed state, with more blocks than the first wrote
+    sim.step(4)
+    out.fill_(float("nan"))
+    rc = lib.flame_reduce_static(sim._ctx, 600, ctypes.c_void_p(out.data_ptr()))
+    assert rc == FLAME_OK
+    torch.cuda.synchronize()
     second = out.cpu().numpy().copy()
-    _compare(second, sim.reduce())
+    ref = sim.reduce()
+    _compare(second, ref, n3, ref["u_max"], b_scale)
     assert not np.allclose(first[7:11], second[7:11], rtol=1e-9)  # the state did change
 
     # beyond the capacity of the scratch array: a clear parameter error
