@@ -93,7 +93,8 @@ typedef struct {
     int strict_cfl;   /* 1: flame_init fails with FLAME_ERR_CFL if pi d_i max(V_A,|u|) > 1 */
     int graph_steps;  /* 0: one kernel launch per step; even G > 0: flame_step replays a
                          captured CUDA graph of G steps for each whole chunk of G steps
-                         (removes launch overhead on small lattices)                    */
+                         (removes launch overhead on small lattices); flame_create
+                         captures the graph that starts at parity 0                      */
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
     int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant), nx a
@@ -157,9 +158,18 @@ flame_status flame_create(flame_ctx **out, const flame_params *p, void *d_state,
 flame_status flame_init(flame_ctx *ctx, const double *d_rho, const double *d_u, const double *d_B,
                         const double *d_gradu, const double *d_gradB);
 
+/* flame_init from FP32 fields: the same initial populations, with d_rho,
+ * d_u, d_B, d_gradu, d_gradB given as FP32 device arrays of the same layout
+ * (half the bytes a caller moves to the device).  Gradients are taken in
+ * FP64 from the FP32 values; the per-site arithmetic is that of flame_init.
+ * Errors and synchronisation as flame_init. */
+flame_status flame_init_f32(flame_ctx *ctx, const float *d_rho, const float *d_u, const float *d_B,
+                            const float *d_gradu, const float *d_gradB);
+
 /* Advance n >= 0 time steps, one fused kernel launch per step (or, with
- * graph_steps = G, graph replays of G launches; the graph is captured on the
- * first use for each starting parity, on a private stream): moments
+ * graph_steps = G, graph replays of G launches; the graph starting at
+ * parity 0 is captured by flame_create, the other on its first use, each on
+ * a private stream): moments
  * (eqs. LB_moments2, mag_field_LB), current from the 3x3 Hall system (eqs.
  * LB_density_current, soe_current_density), central-moment fluid collision
  * (eqs. cm_collision_step, collision_matrix), Hall-equilibrium BGK magnetic
@@ -178,6 +188,11 @@ flame_status flame_info(flame_ctx *ctx, flame_info_t *out);
  * rho [N3], u [3][N3], B [3][N3], J [3][N3] (J from the Hall linear system,
  * as in the step).  Any pointer may be NULL.  Asynchronous. */
 flame_status flame_moments(flame_ctx *ctx, double *d_rho, double *d_u, double *d_B, double *d_J);
+
+/* flame_moments written as FP32 (the precision the per-site arithmetic of
+ * 16-bit storage has; FP32 storage rounds its FP64 per-site moments): rho
+ * [N3], u [3][N3], B [3][N3], J [3][N3], any may be NULL.  Asynchronous. */
+flame_status flame_moments_f32(flame_ctx *ctx, float *d_rho, float *d_u, float *d_B, float *d_J);
 
 /* Moments at a list of sites, for time series such as the velocity at a
  * fixed point that Sec. 4.1-4.2 follow: d_sites [nsites] linear site indices
@@ -205,6 +220,43 @@ flame_status flame_reduce(flame_ctx *ctx, double *h_scalars);
  * FFTs by cuFFT (FP64), shell sums in FP64.  Either output may be NULL.
  * Synchronises. */
 flame_status flame_spectra(flame_ctx *ctx, int nshell, double *h_Eu, double *h_Eb);
+
+/* Magnetic energy in a band of shells (the spectra of Sec. 4.4) and its
+ * gradient, the loss of the differentiable runs:
+ *   L = sum_{lo <= n <= hi} E_B(n),  E_B(n) = 1/2 sum_{round|m| = n} |F(B)(m)|^2,
+ * F(B) = N3^-1 FFT(B) (shell 0 is the mean field; lo >= 1 leaves it out).
+ * d_B: [3][N3] FP64 field (device), or NULL for the B of the current state.
+ * h_L (host, required) receives L.  d_dLdB (device, [3][N3] FP64, may be
+ * NULL) receives dL/dB = N3^-1 Re IFFT(mask F(B)).  d_adj (device, [48][N3]
+ * FP32, may be NULL) receives the seed of flame_step_adjoint for a loss of
+ * the current state: dL/df of the pre-collision populations in natural slot
+ * order, 0 for the fluid and dL/dB_b for every D3Q7 velocity of component b
+ * (B_b is their sum, eq. mag_field_LB).  cuFFT (FP64).  The first call
+ * allocates a workspace (3 N3 doubles and 3 half spectra).  Synchronises.
+ * Errors: FLAME_ERR_PARAM (lo < 0, hi < lo, h_L NULL), FLAME_ERR_STATE (no
+ * flame_init and d_B NULL), FLAME_ERR_CUDA, sticky errors. */
+flame_status flame_band_energy(flame_ctx *ctx, int lo, int hi, const double *d_B, double *h_L, double *d_dLdB,
+                               float *d_adj);
+
+/* Wavenumber energy budget of eq. mhd_en_trans (Sec. 4.4) of fields u, B:
+ *   S(n) = sum_{round|m| < n} Re[F(u)* . (F(u.grad u) - F(J x B))
+ *                                - F(B)* . F(curl(V x B))]
+ *   D(n) = sum_{round|m| < n} k^2 (nu |F(u)|^2 + eta |F(B)|^2)
+ *   E(n) = 1/2 sum_{round|m| = n} (|F(u)|^2 + |F(B)|^2)
+ * with F = N3^-1 FFT, k = 2 pi m / N, spectral derivatives (the Nyquist
+ * wavenumber of an even axis set to zero, also in k^2), J = curl B spectral,
+ * V = u - d_i J (the Hall term in the induction flux; V = u for d_i = 0),
+ * nu = c_s^2 (tau_nu - 1/2), eta = C^2 (tau_eta - 1/2) and d_i of the
+ * context.  Then d/dt sum_{n' < n} E(n') = -S(n) - D(n) for the
+ * incompressible equations.  d_u, d_B: [3][N3] FP64 device fields, or both
+ * NULL for the moments of the current state.  h_E, h_S, h_D: nshell host
+ * doubles each (any may be NULL), 1 <= nshell <= 1024.  cuFFT (FP64): 24
+ * transforms.  The first call allocates a workspace of 15 N3 doubles and 9
+ * half spectra.  Synchronises.  Errors: FLAME_ERR_PARAM (nshell, only one of
+ * d_u / d_B given), FLAME_ERR_STATE (no flame_init and no fields),
+ * FLAME_ERR_CUDA, sticky errors. */
+flame_status flame_energy_budget(flame_ctx *ctx, int nshell, const double *d_u, const double *d_B, double *h_E,
+                                 double *h_S, double *h_D);
 
 /* Copy the raw population state (flame_state_bytes) to d_dst, with the step
  * count and parity needed to resume.  Asynchronous. */

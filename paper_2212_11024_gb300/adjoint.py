@@ -2,7 +2,8 @@
 
 The loss is the magnetic energy in a band of spectral shells at the last
 step, L = sum_{lo <= n <= hi} E_B(n) with E_B(n) = 1/2 sum_{round|m| = n}
-|B_hat(m)|^2 and B_hat = FFT(B) / N3 (the spectra of Sec. 4.4).  Its
+|B_hat(m)|^2 and B_hat = FFT(B) / N3 (the spectra of Sec. 4.4), evaluated
+with its seed dL/df by the library (flame_band_energy).  Its
 gradient with respect to the initial magnetic field, the initial velocity
 and the Hall length d_i comes from the library's hand-written adjoints
 (flame_step_adjoint, flame_init_adjoint), run backwards over the stored
@@ -19,22 +20,6 @@ import math
 import torch
 
 from .flame import Flame, _check, library
-
-
-def band_energy_and_seed(B, lo, hi):
-    """L and dL/dB for L = sum_{lo<=n<=hi} E_B(n) of B [3, nz, ny, nx] (FP64, any device)."""
-    shape = B.shape[1:]
-    n3 = float(shape[0] * shape[1] * shape[2])
-    dev = B.device
-    mz = torch.fft.fftfreq(shape[0], 1.0 / shape[0], dtype=torch.float64, device=dev)[:, None, None]
-    my = torch.fft.fftfreq(shape[1], 1.0 / shape[1], dtype=torch.float64, device=dev)[None, :, None]
-    mx = torch.fft.fftfreq(shape[2], 1.0 / shape[2], dtype=torch.float64, device=dev)[None, None, :]
-    shell = torch.round(torch.sqrt(mx * mx + my * my + mz * mz))
-    mask = ((shell >= lo) & (shell <= hi)).to(torch.float64)
-    Bh = torch.fft.fftn(B, dim=(1, 2, 3))
-    L = 0.5 * (mask * (Bh.real ** 2 + Bh.imag ** 2)).sum() / (n3 * n3)
-    seed = torch.fft.ifftn(mask * Bh, dim=(1, 2, 3)).real / n3
-    return L, seed
 
 
 class _Run:
@@ -57,16 +42,15 @@ class _Run:
             sim.step(1)
         sim.sync()
         self.nsteps = nsteps
-        B = sim.moments()["B"]
-        L, seed = band_energy_and_seed(B, *band)
+        # the loss of the last state and the adjoint seed dL/df (flame_band_energy)
+        L, _, seed = sim.band_energy(band[0], band[1], adjoint_seed=True)
         return L, seed
 
     def backward(self, u0, B0, seed):
         sim = self.sim
         lib = library()
         dev = sim.device
-        lam = torch.zeros((48, self.n3), dtype=torch.float32, device=dev)
-        lam[27:] = seed.reshape(3, 1, self.n3).expand(3, 7, self.n3).reshape(21, self.n3).to(torch.float32)
+        lam = seed.clone()
         other = torch.empty_like(lam)
         ddi = torch.zeros(1, dtype=torch.float64, device=dev)
         ddi_total = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -116,7 +100,7 @@ class FlameBandEnergy(torch.autograd.Function):
         L, seed = run.forward(u0, B0, int(nsteps), tuple(band))
         ctx.run = run
         ctx.save_for_backward(u0, B0, seed)
-        return L.detach().clone()
+        return torch.tensor(L, dtype=torch.float64, device=B0.device)
 
     @staticmethod
     def backward(ctx, gL):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libflame.so")
 SOURCES = ["step.cu", "step_row.cu", "step_row_bgk.cu", "step_row_emhd.cu", "step_row_fd.cu", "diag.cu",
-           "adjoint.cu", "api.cu", "reduce_static.cu"]
+           "adjoint.cu", "api.cu", "reduce_static.cu", "spectral.cu"]
 HEADERS = ["lattice.cuh", "aa.cuh", "step_row.cuh", "flame_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -54,6 +54,7 @@ struct flame_ctx {
   flame::StepConsts k;
   flame::Grid g;
   unsigned stall_tries;  // > 0: the next flame_step runs the wait-failure test (flame_debug_stall_next_step)
+  void* spectral;        // workspace of the spectral diagnostics (spectral.cu), lazily allocated
 };
 
 namespace {
@@ -173,12 +174,19 @@ int flame_ctx_view(const flame_ctx* c, flame::CtxView* v) {
   v->g = c->g;
   v->k = c->k;
   for (int a = 0; a < 3; ++a) v->Bref[a] = c->p.B_ref[a];
+  v->tau_nu = c->p.tau_nu;
+  v->tau_eta = c->p.tau_eta;
+  v->d_i = c->p.d_i;
   return 0;
 }
 
 int flame_ctx_cuda_fail(flame_ctx* c, cudaError_t e) { return (int)cuda_fail(c, e); }
 
+void** flame_ctx_spectral_slot(flame_ctx* c) { return c ? &c->spectral : nullptr; }
+
 extern "C" {
+
+static cudaError_t capture_graph(flame_ctx* c, int parity);
 
 size_t flame_state_bytes(const flame_params* p) {
   if (check_params(p) != FLAME_OK) return 0;
@@ -224,13 +232,23 @@ flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state,
   c->g.ny = p->ny;
   c->g.nz = p->nz;
   c->g.n3 = (long long)p->nx * p->ny * p->nz;
+  // The graph of the first G steps after flame_init (parity 0) is captured
+  // here, with the context, so that the first flame_step does not pay for
+  // the capture; the parity-1 graph is captured on its first use.
+  if (p->graph_steps > 0 && capture_graph(c, 0) != cudaSuccess) {
+    flame_destroy(c);
+    return FLAME_ERR_CUDA;
+  }
   *out = c;
   return FLAME_OK;
 }
 
-flame_status flame_init(flame_ctx* c, const double* d_rho, const double* d_u, const double* d_B,
-                        const double* d_gradu, const double* d_gradB) {
-  const Range range("flame_init");
+}  // extern "C"
+
+// flame_init and flame_init_f32: the fields' element type F (double or float).
+template <class F>
+static flame_status init_from(flame_ctx* c, const F* d_rho, const F* d_u, const F* d_B, const F* d_gradu,
+                              const F* d_gradB) {
   if (!c) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
   if (!d_u || !d_B) return FLAME_ERR_PARAM;
@@ -239,8 +257,12 @@ flame_status flame_init(flame_ctx* c, const double* d_rho, const double* d_u, co
   c->nonfinite = 0;
   cudaError_t e = cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
-  e = flame::launch_init(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu, d_gradB,
-                         c->d_flags + 1, c->stream);
+  if constexpr (sizeof(F) == sizeof(double))
+    e = flame::launch_init(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu, d_gradB,
+                           c->d_flags + 1, c->stream);
+  else
+    e = flame::launch_init_f32(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu,
+                               d_gradB, c->d_flags + 1, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   unsigned bits = 0;
   e = cudaMemcpyAsync(&bits, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
@@ -260,6 +282,20 @@ flame_status flame_init(flame_ctx* c, const double* d_rho, const double* d_u, co
   }
   if (c->p.strict_cfl && c->cfl > 1.0) return FLAME_ERR_CFL;
   return FLAME_OK;
+}
+
+extern "C" {
+
+flame_status flame_init(flame_ctx* c, const double* d_rho, const double* d_u, const double* d_B,
+                        const double* d_gradu, const double* d_gradB) {
+  const Range range("flame_init");
+  return init_from<double>(c, d_rho, d_u, d_B, d_gradu, d_gradB);
+}
+
+flame_status flame_init_f32(flame_ctx* c, const float* d_rho, const float* d_u, const float* d_B,
+                            const float* d_gradu, const float* d_gradB) {
+  const Range range("flame_init_f32");
+  return init_from<float>(c, d_rho, d_u, d_B, d_gradu, d_gradB);
 }
 
 // Capture graph_steps step launches starting at `parity` into c->graph[parity].
@@ -355,6 +391,15 @@ flame_status flame_moments(flame_ctx* c, double* d_rho, double* d_u, double* d_B
   if (!c->initialized) return FLAME_ERR_STATE;
   return cuda_fail(c, flame::launch_moments(c->p.storage, c->parity, c->state, c->g, c->k, d_rho, d_u, d_B, d_J,
                                             c->stream));
+}
+
+flame_status flame_moments_f32(flame_ctx* c, float* d_rho, float* d_u, float* d_B, float* d_J) {
+  const Range range("flame_moments_f32");
+  flame_status st = usable(c);
+  if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  return cuda_fail(c, flame::launch_moments_f32(c->p.storage, c->parity, c->state, c->g, c->k, d_rho, d_u, d_B,
+                                                d_J, c->stream));
 }
 
 flame_status flame_populations(flame_ctx* c, double* d_f) {
@@ -584,6 +629,7 @@ void flame_destroy(flame_ctx* c) {
   cudaFree(c->d_adj_partials);
   cudaFree(c->d_adj_ws);
   cudaFree(c->d_bfield);
+  flame::spectral_ws_free(c->spectral);
   delete c;
 }
 

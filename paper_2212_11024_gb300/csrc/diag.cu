@@ -13,7 +13,8 @@ namespace {
 // or 2^-8 (BF16) relative, far above FP32's 2^-24; gradients are taken in
 // FP64 from the FP64 fields either way.
 
-__device__ __forceinline__ double cdiff(const double* F, int a, int x, int y, int z, const Grid& g) {
+template <class F>
+__device__ __forceinline__ double cdiff(const F* f, int a, int x, int y, int z, const Grid& g) {
   int xp = x, xm = x, yp = y, ym = y, zp = z, zm = z;
   if (a == 0) {
     xp = x + 1 == g.nx ? 0 : x + 1;
@@ -25,14 +26,15 @@ __device__ __forceinline__ double cdiff(const double* F, int a, int x, int y, in
     zp = z + 1 == g.nz ? 0 : z + 1;
     zm = z == 0 ? g.nz - 1 : z - 1;
   }
-  return 0.5 * (F[((long long)zp * g.ny + yp) * g.nx + xp] - F[((long long)zm * g.ny + ym) * g.nx + xm]);
+  return 0.5 * ((double)f[((long long)zp * g.ny + yp) * g.nx + xp] - (double)f[((long long)zm * g.ny + ym) * g.nx + xm]);
 }
 
-template <class T, class R>
-__global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq, const double* __restrict__ rho_f,
-                            const double* __restrict__ u, const double* __restrict__ Bf,
-                            const double* __restrict__ gu, const double* __restrict__ gB,
-                            unsigned* __restrict__ speed_bits) {
+// F: the element type of the caller's fields (FP64 for flame_init, FP32 for
+// flame_init_f32).
+template <class T, class R, class F>
+__global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq, const F* __restrict__ rho_f,
+                            const F* __restrict__ u, const F* __restrict__ Bf, const F* __restrict__ gu,
+                            const F* __restrict__ gB, unsigned* __restrict__ speed_bits) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -195,9 +197,11 @@ struct SiteReal<float> {
   using type = double;
 };
 
-template <class T, bool ODD>
-__global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, double* __restrict__ rho,
-                               double* __restrict__ u, double* __restrict__ B, double* __restrict__ J) {
+// O: the element type of the outputs (FP64 for flame_moments, FP32 for
+// flame_moments_f32).
+template <class T, bool ODD, class O>
+__global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, O* __restrict__ rho,
+                               O* __restrict__ u, O* __restrict__ B, O* __restrict__ J) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -208,11 +212,11 @@ __global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, 
   R sf[kQ], sg[3][kM];
   load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
   const SiteMoments<R> m = site_moments(sf, sg, k);
-  if (rho) rho[site] = m.rho(k);
+  if (rho) rho[site] = (O)m.rho(k);
   for (int a = 0; a < 3; ++a) {
-    if (u) u[a * g.n3 + site] = (double)m.U[a];
-    if (B) B[a * g.n3 + site] = m.B(k, a);
-    if (J) J[a * g.n3 + site] = (double)m.J[a];
+    if (u) u[a * g.n3 + site] = (O)m.U[a];
+    if (B) B[a * g.n3 + site] = (O)m.B(k, a);
+    if (J) J[a * g.n3 + site] = (O)m.J[a];
   }
 }
 
@@ -352,15 +356,49 @@ __global__ void reduce_final_kernel(const double* __restrict__ partials, int nbl
 // Block of `threads` threads: x-rows of up to `threads` sites, several
 // rows per block when nx is small.
 
-template <class T>
-cudaError_t moments_t(int odd, const void* pop, Grid g, const StepConsts& k, double* rho, double* u, double* B,
-                      double* J, cudaStream_t s) {
+template <class T, class O>
+cudaError_t moments_t(int odd, const void* pop, Grid g, const StepConsts& k, O* rho, O* u, O* B, O* J,
+                      cudaStream_t s) {
   const dim3 b = site_block(g), gr = site_grid(g, b);
   if (odd)
-    moments_kernel<T, true><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
+    moments_kernel<T, true, O><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
   else
-    moments_kernel<T, false><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
+    moments_kernel<T, false, O><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
   return cudaGetLastError();
+}
+
+template <class F>
+cudaError_t init_t(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const F* rho, const F* u,
+                   const F* B, const F* gu, const F* gB, unsigned* speed_bits, cudaStream_t s) {
+  const dim3 b = site_block(g), gr = site_grid(g, b);
+  switch (storage) {
+    case 1:
+      init_kernel<float, double, F><<<gr, b, 0, s>>>(static_cast<float*>(pop), g, k, noneq, rho, u, B, gu, gB,
+                                                      speed_bits);
+      break;
+    case 2:
+      init_kernel<__half, float, F><<<gr, b, 0, s>>>(static_cast<__half*>(pop), g, k, noneq, rho, u, B, gu, gB,
+                                                      speed_bits);
+      break;
+    case 3:
+      init_kernel<__nv_bfloat16, float, F><<<gr, b, 0, s>>>(static_cast<__nv_bfloat16*>(pop), g, k, noneq, rho, u,
+                                                             B, gu, gB, speed_bits);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class O>
+cudaError_t moments_any(int storage, int odd, const void* pop, Grid g, const StepConsts& k, O* rho, O* u, O* B,
+                        O* J, cudaStream_t s) {
+  switch (storage) {
+    case 1: return moments_t<float, O>(odd, pop, g, k, rho, u, B, J, s);
+    case 2: return moments_t<__half, O>(odd, pop, g, k, rho, u, B, J, s);
+    case 3: return moments_t<__nv_bfloat16, O>(odd, pop, g, k, rho, u, B, J, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <class T>
@@ -390,24 +428,23 @@ cudaError_t reduce_t(int odd, const void* pop, Grid g, const StepConsts& k, int 
 cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
                         const double* u, const double* B, const double* gu, const double* gB,
                         unsigned* speed_bits, cudaStream_t s) {
-  const dim3 b = site_block(g), gr = site_grid(g, b);
-  switch (storage) {
-    case 1: init_kernel<float, double><<<gr, b, 0, s>>>(static_cast<float*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    case 2: init_kernel<__half, float><<<gr, b, 0, s>>>(static_cast<__half*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    case 3: init_kernel<__nv_bfloat16, float><<<gr, b, 0, s>>>(static_cast<__nv_bfloat16*>(pop), g, k, noneq, rho, u, B, gu, gB, speed_bits); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return init_t<double>(storage, pop, g, k, noneq, rho, u, B, gu, gB, speed_bits, s);
+}
+
+cudaError_t launch_init_f32(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const float* rho,
+                            const float* u, const float* B, const float* gu, const float* gB,
+                            unsigned* speed_bits, cudaStream_t s) {
+  return init_t<float>(storage, pop, g, k, noneq, rho, u, B, gu, gB, speed_bits, s);
 }
 
 cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* rho,
                            double* u, double* B, double* J, cudaStream_t s) {
-  switch (storage) {
-    case 1: return moments_t<float>(odd, pop, g, k, rho, u, B, J, s);
-    case 2: return moments_t<__half>(odd, pop, g, k, rho, u, B, J, s);
-    case 3: return moments_t<__nv_bfloat16>(odd, pop, g, k, rho, u, B, J, s);
-  }
-  return cudaErrorInvalidValue;
+  return moments_any<double>(storage, odd, pop, g, k, rho, u, B, J, s);
+}
+
+cudaError_t launch_moments_f32(int storage, int odd, const void* pop, Grid g, const StepConsts& k, float* rho,
+                               float* u, float* B, float* J, cudaStream_t s) {
+  return moments_any<float>(storage, odd, pop, g, k, rho, u, B, J, s);
 }
 
 cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* f,

@@ -59,8 +59,16 @@ cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int
                         const double* u, const double* B, const double* gu, const double* gB,
                         unsigned* speed_bits, cudaStream_t s);
 
+// The same from FP32 fields (flame_init_f32).
+cudaError_t launch_init_f32(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const float* rho,
+                            const float* u, const float* B, const float* gu, const float* gB,
+                            unsigned* speed_bits, cudaStream_t s);
+
 cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* rho,
                            double* u, double* B, double* J, cudaStream_t s);
+// The same, written as FP32 (flame_moments_f32).
+cudaError_t launch_moments_f32(int storage, int odd, const void* pop, Grid g, const StepConsts& k, float* rho,
+                               float* u, float* B, float* J, cudaStream_t s);
 
 cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, const StepConsts& k,
                                double* f, cudaStream_t s);
@@ -96,6 +104,7 @@ struct CtxView {
   Grid g;
   StepConsts k;
   double Bref[3];
+  double tau_nu, tau_eta, d_i;  // the context's parameters in FP64
 };
 
 // Adjoint kernels (adjoint.cu).  The step adjoint reads the forward state at
@@ -118,6 +127,12 @@ cudaError_t launch_shell_bin(const void* spec /* cufftDoubleComplex */, Grid g, 
 struct flame_ctx;
 // Fills *v from the context; returns 0, or -1 for a null context.
 int flame_ctx_view(const flame_ctx* c, flame::CtxView* v);
+// The context's slot for the spectral diagnostics' workspace (spectral.cu),
+// released by flame_destroy through flame::spectral_ws_free.
+void** flame_ctx_spectral_slot(flame_ctx* c);
+namespace flame {
+void spectral_ws_free(void* ws);
+}
 // Records a failed CUDA call in the context's sticky status, as the entry
 // points of api.cu do (FLAME_ERR_CUDA unless an error is already recorded);
 // returns FLAME_ERR_CUDA, or FLAME_OK for e == cudaSuccess.

@@ -93,6 +93,10 @@ def _lib():
             "flame_step_adjoint": (i, [vp, vp, i, vp, vp, vp]),
             "flame_init_adjoint": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "flame_debug_stall_next_step": (i, [vp, ctypes.c_uint]),
+            "flame_init_f32": (i, [vp, vp, vp, vp, vp, vp]),
+            "flame_moments_f32": (i, [vp, vp, vp, vp, vp]),
+            "flame_band_energy": (i, [vp, i, i, vp, P(d), vp, vp]),
+            "flame_energy_budget": (i, [vp, i, vp, vp, P(d), P(d), P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -196,14 +200,16 @@ class Flame:
         self._lib = lib
 
     # ------------------------------------------------------------------ util
-    def _dev(self, a, ncomp):
-        """FP64 contiguous device tensor of shape [ncomp, nz, ny, nx] (or [nz,ny,nx])."""
+    def _dev(self, a, ncomp, dtype=None):
+        """Contiguous device tensor (FP64 unless dtype says otherwise) of shape
+        [ncomp, nz, ny, nx] (or [nz,ny,nx])."""
         if a is None:
             return None
         t = self.torch
+        dtype = t.float64 if dtype is None else dtype
         if isinstance(a, np.ndarray):
-            a = t.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
-        a = a.to(device=self.device, dtype=t.float64).contiguous()
+            a = t.from_numpy(np.ascontiguousarray(a))
+        a = a.to(device=self.device, dtype=dtype).contiguous()
         want = (ncomp,) + self.shape if ncomp else self.shape
         if tuple(a.shape) != want:
             raise ValueError(f"expected shape {want}, got {tuple(a.shape)}")
@@ -242,16 +248,21 @@ class Flame:
 
     # ------------------------------------------------------------------- API
     def init(self, rho, u, B, gradu=None, gradB=None):
-        """flame_init from FP64 fields (numpy or torch): rho [nz,ny,nx] or None,
-        u, B [3,nz,ny,nx], optional gradients [9,nz,ny,nx]."""
-        r, uu, bb = self._dev(rho, 0), self._dev(u, 3), self._dev(B, 3)
-        gu, gb = self._dev(gradu, 9), self._dev(gradB, 9)
+        """flame_init from fields (numpy or torch): rho [nz,ny,nx] or None,
+        u, B [3,nz,ny,nx], optional gradients [9,nz,ny,nx].  FP32 fields (u
+        of dtype float32) go through flame_init_f32 as they are; anything
+        else is converted to FP64 for flame_init."""
+        t = self.torch
+        f32 = (u.dtype == np.float32) if isinstance(u, np.ndarray) else (getattr(u, "dtype", None) is t.float32)
+        dt = t.float32 if f32 else t.float64
+        r, uu, bb = self._dev(rho, 0, dt), self._dev(u, 3, dt), self._dev(B, 3, dt)
+        gu, gb = self._dev(gradu, 9, dt), self._dev(gradB, 9, dt)
         cur = self._before()
         # flame_init synchronises the library's stream, so the temporaries outlive their use
-        rc = self._lib.flame_init(self._ctx_or_raise(), self._ptr(r), self._ptr(uu), self._ptr(bb),
-                                  self._ptr(gu), self._ptr(gb))
+        fn = self._lib.flame_init_f32 if f32 else self._lib.flame_init
+        rc = fn(self._ctx_or_raise(), self._ptr(r), self._ptr(uu), self._ptr(bb), self._ptr(gu), self._ptr(gb))
         self._after(cur)
-        _check(rc, "flame_init")
+        _check(rc, "flame_init_f32" if f32 else "flame_init")
 
     def step(self, n=1):
         _check(self._lib.flame_step(self._ctx_or_raise(), int(n)), "flame_step")
@@ -264,19 +275,27 @@ class Flame:
         _check(self._lib.flame_info(self._ctx_or_raise(), ctypes.byref(inf)), "flame_info")
         return dict(step=inf.step, parity=inf.parity, nonfinite=inf.nonfinite, cfl=inf.cfl, max_speed=inf.max_speed)
 
-    def moments(self, out=None) -> dict:
-        """rho, u, B, J of the current pre-collision populations (FP64 CUDA tensors)."""
+    def moments(self, out=None, dtype=None) -> dict:
+        """rho, u, B, J of the current pre-collision populations as CUDA
+        tensors: FP64 (flame_moments) or, with dtype=torch.float32 or FP32
+        tensors in `out`, FP32 (flame_moments_f32)."""
         t = self.torch
         if out is None:
-            out = dict(rho=t.empty(self.shape, dtype=t.float64, device=self.device),
-                       u=t.empty((3,) + self.shape, dtype=t.float64, device=self.device),
-                       B=t.empty((3,) + self.shape, dtype=t.float64, device=self.device),
-                       J=t.empty((3,) + self.shape, dtype=t.float64, device=self.device))
+            dt = t.float64 if dtype is None else dtype
+            out = dict(rho=t.empty(self.shape, dtype=dt, device=self.device),
+                       u=t.empty((3,) + self.shape, dtype=dt, device=self.device),
+                       B=t.empty((3,) + self.shape, dtype=dt, device=self.device),
+                       J=t.empty((3,) + self.shape, dtype=dt, device=self.device))
+        dts = {v.dtype for v in out.values() if v is not None}
+        if len(dts) != 1 or not dts <= {t.float32, t.float64}:
+            raise ValueError("moments: outputs must be all FP32 or all FP64")
+        f32 = dts == {t.float32}
+        fn = self._lib.flame_moments_f32 if f32 else self._lib.flame_moments
         cur = self._before()
-        rc = self._lib.flame_moments(self._ctx_or_raise(), self._ptr(out.get("rho")), self._ptr(out.get("u")),
-                                     self._ptr(out.get("B")), self._ptr(out.get("J")))
+        rc = fn(self._ctx_or_raise(), self._ptr(out.get("rho")), self._ptr(out.get("u")), self._ptr(out.get("B")),
+                self._ptr(out.get("J")))
         self._after(cur, *out.values())
-        _check(rc, "flame_moments")
+        _check(rc, "flame_moments_f32" if f32 else "flame_moments")
         return out
 
     def probe(self, sites, out=None):
@@ -330,6 +349,37 @@ class Flame:
         Eb = (ctypes.c_double * nshell)()
         _check(self._lib.flame_spectra(self._ctx_or_raise(), int(nshell), Eu, Eb), "flame_spectra")
         return np.array(Eu[:]), np.array(Eb[:])
+
+    def band_energy(self, lo, hi, B=None, grad=False, adjoint_seed=False):
+        """flame_band_energy: L = sum_{lo<=n<=hi} E_B(n) of the current state
+        (or of the FP64 field B [3,nz,ny,nx]); with grad, also dL/dB (FP64
+        CUDA [3,nz,ny,nx]); with adjoint_seed, also the FP32 [48, N3] seed of
+        flame_step_adjoint.  Returns (L, dLdB or None, seed or None)."""
+        t = self.torch
+        bb = self._dev(B, 3)
+        g = t.empty((3,) + self.shape, dtype=t.float64, device=self.device) if grad else None
+        a = t.empty((48, self.n3), dtype=t.float32, device=self.device) if adjoint_seed else None
+        L = ctypes.c_double()
+        cur = self._before()
+        rc = self._lib.flame_band_energy(self._ctx_or_raise(), int(lo), int(hi), self._ptr(bb), ctypes.byref(L),
+                                         self._ptr(g), self._ptr(a))
+        self._after(cur, g, a)
+        _check(rc, "flame_band_energy")
+        return float(L.value), g, a
+
+    def energy_budget(self, nshell, u=None, B=None):
+        """flame_energy_budget: (E, S, D) numpy FP64 [nshell] of the current
+        state's u, B (or of the given FP64 fields), with this context's nu,
+        eta and d_i."""
+        if (u is None) != (B is None):
+            raise ValueError("energy_budget: give both u and B, or neither")
+        uu, bb = self._dev(u, 3), self._dev(B, 3)
+        E, S, D = (ctypes.c_double * nshell)(), (ctypes.c_double * nshell)(), (ctypes.c_double * nshell)()
+        cur = self._before()
+        rc = self._lib.flame_energy_budget(self._ctx_or_raise(), int(nshell), self._ptr(uu), self._ptr(bb), E, S, D)
+        self._after(cur)
+        _check(rc, "flame_energy_budget")
+        return np.array(E[:]), np.array(S[:]), np.array(D[:])
 
     def debug_stall_next_step(self, tries=1024):
         """Arm the wait-failure test for the next step (flame_debug_stall_next_step):

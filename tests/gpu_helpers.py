@@ -23,6 +23,13 @@ def rel_dev_err(f_gpu, f_ref, f_rest, sl=slice(None)):
     return d / n
 
 
+def slot_dev_errs(f_gpu, f_ref, f_rest):
+    """Per population slot: ||f_gpu - f_ref|| / ||f_ref - f_rest|| ([48])."""
+    d = np.sqrt(((f_gpu - f_ref) ** 2).reshape(f_ref.shape[0], -1).sum(1))
+    n = np.sqrt(((f_ref - f_rest) ** 2).reshape(f_ref.shape[0], -1).sum(1))
+    return d / np.maximum(n, 1e-300)
+
+
 def rel_l2(x, ref):
     return float(np.linalg.norm(np.ravel(x - ref)) / np.linalg.norm(np.ravel(ref)))
 

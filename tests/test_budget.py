@@ -1,13 +1,13 @@
-"""Energy budget of Sec. 4.4: the GPU-side torch implementation against the
-numpy FP64 oracle implementation (on CPU tensors here), and the properties the
-mathematics fixes: for spectrally solenoidal fields the nonlinear flux through
-a sphere enclosing every mode vanishes (energy conservation of the ideal
-terms, with or without the Hall term), and E sums to the total energy."""
+"""Properties of the oracle's energy budget (Sec. 4.4) that the mathematics
+fixes: for spectrally solenoidal fields the nonlinear flux through a sphere
+enclosing every mode vanishes (energy conservation of the ideal terms, with
+or without the Hall term), and E sums to the total energy; the Orszag-Tang
+fields put energy in shells 1 and 2 only, with no flux (a steady Euler
+flow).  The library's implementation is compared with this one on the GPU
+(tests/test_gpu_spectral.py)."""
 import numpy as np
-import torch
 
 from oracle import spectra as S
-from paper_2212_11024_gb300 import budget as Bd
 from paper_2212_11024_gb300 import inputs as I
 
 
@@ -29,17 +29,13 @@ def _spectral_solenoidal(F):
     return np.stack([np.real(np.fft.ifftn(Fh[c])) for c in range(3)])
 
 
-def test_budget_matches_numpy_oracle_and_invariants():
+def test_budget_flux_vanishes_for_solenoidal_fields():
     shape = (12, 10, 16)
     u, B = I.turbulence(shape, 4, 5, 0.05, 0.05, shells=(1, 3))
     u, B = _spectral_solenoidal(u), _spectral_solenoidal(B)
     nsh = 13  # every shell of this grid is < 12, so S(12) encloses all modes
     for di in (0.0, 1.5):
-        E, Sf, D = [x.numpy() for x in Bd.energy_budget(torch.tensor(u), torch.tensor(B), 0.01, 0.02, nsh, di)]
         E0, S0, D0 = S.energy_budget(u, B, 0.01, 0.02, nsh, di)
-        assert np.allclose(E, E0, rtol=1e-12, atol=1e-18)
-        assert np.allclose(Sf, S0, rtol=1e-10, atol=1e-16)
-        assert np.allclose(D, D0, rtol=1e-12, atol=1e-18)
         assert abs(S0[-1]) < 1e-12 * np.abs(S0).max()
         assert np.abs(S0).max() > 1e-8  # the fluxes themselves are not trivial
     Etot = 0.5 * ((u * u).sum(0).mean() + (B * B).sum(0).mean())

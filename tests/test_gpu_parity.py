@@ -14,8 +14,8 @@ the whole field B, so its relative error is ~|B|/|J| times larger than
 that of B: 5e-6 after 20 steps.  Field tolerances for the 200-step wave are
 the ones the method's accuracy budget allows (1e-5 relative L2).  FP16 and
 BF16 storage round each stored deviation to 11 and 8 significant bits;
-their per-field tolerances (2e-2, 1e-1 at 100 steps) are stated in the
-tests.
+their per-field tolerances (about three times the errors measured on GB300)
+are stated in the tests.
 """
 import numpy as np
 import pytest
@@ -91,17 +91,25 @@ def test_wave_config1_fp32():
     assert rel_l2(mg["u"], ue) < 3.5e-2 and rel_l2(mg["B"] - bz, Be - bz) < 5e-2
 
 
-@pytest.mark.parametrize("storage,tol", [("fp16", 2e-2), ("bf16", 1e-1)])
-def test_reduced_storage_vs_oracle(storage, tol):
+# FP16 / BF16 after 100 turbulence steps: about three times the errors
+# measured on GB300 (FP16: u 7.1e-4, B 1.3e-3, J 4.5e-3, rho 5.8e-5; BF16:
+# u 5.6e-3, B 9.7e-3, J 3.3e-2, rho 5.1e-4).
+REDUCED_TOL = {"fp16": dict(u=2e-3, B=4e-3, J=1.4e-2, rho=2e-4),
+               "bf16": dict(u=1.7e-2, B=3e-2, J=0.1, rho=1.5e-3)}
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reduced_storage_vs_oracle(storage):
     """FP16 / BF16 deviation storage with FP32 collision, 100 steps of
     shell-limited turbulence (rms 0.05, tau 0.51), per-field relative L2
-    against the FP64 oracle."""
+    against the FP64 oracle (density absolute), at REDUCED_TOL."""
     shape = (24, 24, 24)
+    tol = REDUCED_TOL[storage]
     u, B = turbulence(shape, 9, 0.05, shells=(1, 4))
     fg, mg, fo, mo = run_both(shape, 0.51, 0.51, 0.05 * 24, u, B, 100, storage=storage, literal=False)
     for k in ("u", "B", "J"):
-        assert rel_l2(mg[k], mo[k]) < tol, (k, rel_l2(mg[k], mo[k]))
-    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-3
+        assert rel_l2(mg[k], mo[k]) < tol[k], (k, rel_l2(mg[k], mo[k]))
+    assert np.abs(mg["rho"] - mo["rho"]).max() < tol["rho"]
 
 
 def test_reduce_and_spectra_match_oracle():
@@ -321,24 +329,27 @@ def test_scheme_variants_match_oracle(variant):
 
 def test_orszag_tang_run_and_energy_budget():
     """Orszag-Tang vortex (Sec. 4.4) at 32^3 (U0 = 0.05/sqrt(3), B0 = 0.8 U0,
-    tau = 0.6), 40 steps through the library; the budget of the resulting
-    fields computed on the GPU (budget.energy_budget on CUDA tensors) equals
-    the numpy FP64 oracle implementation on the same fields."""
-    import torch
+    tau = 0.6), 40 FP32 steps through the library and through the oracle
+    from the same fields; the budget of the library's state
+    (flame_energy_budget) against the budget of the oracle's fields."""
     from oracle import spectra as S
-    from paper_2212_11024_gb300 import Flame, budget, inputs
+    from paper_2212_11024_gb300 import Flame, inputs
     N = 32
     u, B = inputs.orszag_tang((N, N, N), 1.0, 0.8, scale=0.05 / np.sqrt(3.0))
     sim = Flame(N, N, N, 0.6, 0.6, 0.0)
     sim.init(None, u, B)
     sim.step(40)
-    m = sim.moments()
+    E, Sf, D = sim.energy_budget(30)
     sim.close()
+    p = O.Params(N, N, N, 0.6, 0.6, 0.0)
+    pop = O.init(p, None, u, B)
+    O.step(p, pop, 40, literal=False)
+    m = O.moments(p, pop)
     nu, eta = 0.1 / 3, 0.1 / 4
-    E, Sf, D = [x.cpu().numpy() for x in budget.energy_budget(m["u"], m["B"], nu, eta, 30)]
-    E0, S0, D0 = S.energy_budget(m["u"].cpu().numpy(), m["B"].cpu().numpy(), nu, eta, 30)
-    assert np.allclose(E, E0, rtol=1e-12, atol=1e-20)
-    assert np.allclose(Sf, S0, rtol=1e-9, atol=1e-16 * np.abs(S0).max())
-    assert np.allclose(D, D0, rtol=1e-12, atol=1e-20)
+    E0, S0, D0 = S.energy_budget(m["u"], m["B"], nu, eta, 30)
+    big = E0 > 1e-8 * E0.max()
+    assert np.allclose(E[big], E0[big], rtol=1e-5)
+    assert np.abs(Sf - S0).max() < 1e-4 * np.abs(S0).max()
+    assert np.allclose(D[1:], D0[1:], rtol=1e-5)
     # after 40 steps energy has moved beyond the initial shells 1-2
     assert E[3:].sum() > 1e-6 * E.sum()

@@ -8,9 +8,30 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_helpers import rel_dev_err, rel_l2, rest_populations, run_both, turbulence
+from gpu_helpers import rel_dev_err, rel_l2, rest_populations, run_both, slot_dev_errs, turbulence
 
 pytestmark = pytest.mark.gpu
+
+# Tolerances against the FP64 oracle after 21 steps, about three times the
+# largest error measured on GB300 over the lattices of each test (relative
+# L2 of the fluctuations per field, of the population deviations per group
+# and per slot; density absolute).  The current's relative error is larger
+# on lattices a single row or plane thick ("thin"), where the fields vary
+# along one or two axes only and J is small against B.
+TOL = {
+    # storage: u, B, J (bulk), J (thin), rho, fluid pops, magnetic pops, worst slot
+    "fp16": dict(u=1e-3, B=1.2e-3, J=3e-3, J_thin=2.5e-2, rho=3e-4, fluid=1.5e-3, mag=1.5e-3, slot=7e-3),
+    "bf16": dict(u=8e-3, B=1e-2, J=2.5e-2, J_thin=0.2, rho=2e-3, fluid=1.4e-2, mag=1.4e-2, slot=6e-2),
+}
+# the scheme's variants on the row kernel (same 21 steps)
+TOL_VARIANT = {
+    "fp16": dict(u=1.3e-3, B=1.2e-3, J=4.5e-3, J_thin=2.2e-2, rho=3e-4, fluid=2.3e-3, mag=1.6e-3, slot=1.1e-2),
+    "bf16": dict(u=1.1e-2, B=1.1e-2, J=4e-2, J_thin=0.18, rho=2.2e-3, fluid=1.9e-2, mag=1.4e-2, slot=0.1),
+}
+
+
+def _thin(shape):
+    return shape[0] * shape[1] < 6
 
 # (nz, ny, nx): compile-time row lengths 64, 128, 256 and 512 and the general
 # one (192, and 960 / 1024 with 480- / 512-thread blocks); single-row and
@@ -25,28 +46,38 @@ def _fields(shape, seed):
     return u, B + B0[:, None, None, None]
 
 
+def _check_vs_oracle(shape, fg, mg, fo, mo, tol):
+    b0 = B0[:, None, None, None]
+    rest = rest_populations(shape, 1.0, tuple(B0))
+    errs = dict(u=rel_l2(mg["u"], mo["u"]), B=rel_l2(mg["B"] - b0, mo["B"] - b0), J=rel_l2(mg["J"], mo["J"]),
+                rho=float(np.abs(mg["rho"] - mo["rho"]).max()), fluid=rel_dev_err(fg, fo, rest, slice(0, 27)),
+                mag=rel_dev_err(fg, fo, rest, slice(27, 48)), slot=float(slot_dev_errs(fg, fo, rest).max()))
+    for k, e in errs.items():
+        t = tol["J_thin"] if (k == "J" and _thin(shape)) else tol[k]
+        assert e < t, (k, e, t)
+
+
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("storage,tol", [("fp16", 2e-2), ("bf16", 1e-1)])
-def test_row_kernel_vs_oracle(shape, storage, tol):
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_row_kernel_vs_oracle(shape, storage):
     """21 steps (ending on an odd-parity state) of Hall turbulence with a mean
-    field, per-field relative L2 of the fluctuations against the FP64 oracle;
-    density to 1e-3."""
+    field against the FP64 oracle: per field (u, B and J fluctuations,
+    density), per population group (fluid, magnetic) and for the worst single
+    population slot, at the TOL bounds above."""
     u, B = _fields(shape, 41)
     fg, mg, fo, mo = run_both(shape, 0.52, 0.55, 1.5, u, B, 21, storage=storage, literal=False, Bref=tuple(B0))
-    b0 = B0[:, None, None, None]
-    assert rel_l2(mg["u"], mo["u"]) < tol
-    assert rel_l2(mg["B"] - b0, mo["B"] - b0) < tol
-    assert rel_l2(mg["J"], mo["J"]) < tol
-    assert np.abs(mg["rho"] - mo["rho"]).max() < 1e-3
+    _check_vs_oracle(shape, fg, mg, fo, mo, TOL[storage])
 
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("storage,ulps", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
 def test_row_kernel_agrees_with_site_kernel(shape, storage, ulps):
-    """Same fields, 9 steps, kernel "auto" (row kernel) vs "site": both compute
+    """Same fields, 51 steps, kernel "auto" (row kernel) vs "site": both compute
     the collision in FP32 in a different order, so the stored deviations
-    differ by a few units of the storage's last place at some entries -- and
-    do differ somewhere, which shows that the row kernel ran."""
+    differ by a few units of the storage's last place -- and do differ
+    somewhere, which shows that the row kernel ran.  Over 51 steps the
+    largest difference measured on GB300 stays at 4.2 units (at 9 steps 2.1),
+    so the two evaluate the same step; the bound is 12 units."""
     from paper_2212_11024_gb300 import Flame
     nz, ny, nx = shape
     u, B = _fields(shape, 43)
@@ -54,15 +85,14 @@ def test_row_kernel_agrees_with_site_kernel(shape, storage, ulps):
     for kernel in ("auto", "site"):
         sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), kernel=kernel)
         sim.init(None, u, B)
-        sim.step(9)
+        sim.step(51)
         pops.append(sim.populations().cpu().numpy())
         sim.close()
     a, b = pops
     dev = np.abs(b - np.median(b, axis=(1, 2, 3), keepdims=True)).max()
     d = np.abs(a - b)
-    assert d.max() < 8 * ulps * dev, d.max() / dev
+    assert d.max() < 12 * ulps * dev, d.max() / dev
     assert (d > 0).any()
-    assert (d > 0).mean() < 0.5
 
 
 def test_row_kernel_graph_replay_is_bit_identical():
@@ -191,38 +221,32 @@ def _variant_run(shape, storage, kernel, variant, steps, seed):
 
 @pytest.mark.parametrize("shape", VARIANT_SHAPES)
 @pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
-@pytest.mark.parametrize("storage,tol", [("fp16", 2e-2), ("bf16", 1e-1)])
-def test_row_kernel_variants_vs_oracle(shape, variant, storage, tol):
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_row_kernel_variants_vs_oracle(shape, variant, storage):
     """21 steps of each variant with 16-bit storage on the row kernel against
-    the oracle's variant: relative L2 of the population deviations (fluid and
-    magnetic) and of the u and B fluctuations."""
+    the oracle's variant, field by field, per population group and slot, at
+    the TOL_VARIANT bounds above."""
     nz, ny, nx = shape
     u, B, fg, mg = _variant_run(shape, storage, "auto", variant, 21, 51)
     p = O.Params(nx, ny, nz, 0.52, 0.55, 1.5)
     fo = O.init(p, None, u, B)
     O.step_variant(p, fo, 21, variant, literal=False)
     mo = O.moments(p, fo)
-    rest = rest_populations(shape, 1.0, tuple(B0))
-    assert rel_dev_err(fg, fo, rest, slice(0, 27)) < tol
-    assert rel_dev_err(fg, fo, rest, slice(27, 48)) < tol
-    b0 = B0[:, None, None, None]
-    assert rel_l2(mg["u"], mo["u"]) < tol
-    assert rel_l2(mg["B"] - b0, mo["B"] - b0) < tol
+    _check_vs_oracle(shape, fg, mg, fo, mo, TOL_VARIANT[storage])
 
 
 @pytest.mark.parametrize("shape", VARIANT_SHAPES)
 @pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
 def test_row_kernel_variants_agree_with_site_kernel(shape, variant):
-    """FP16, 9 steps of each variant, row kernel vs one-site kernel: a few
-    half-precision units of the last place apart at most, and apart
-    somewhere (the row kernel ran)."""
-    pops = [_variant_run(shape, "fp16", kernel, variant, 9, 53)[2] for kernel in ("auto", "site")]
+    """FP16, 51 steps of each variant, row kernel vs one-site kernel: at most
+    12 half-precision units of the last place apart (4.2 measured on GB300),
+    and apart somewhere (the row kernel ran)."""
+    pops = [_variant_run(shape, "fp16", kernel, variant, 51, 53)[2] for kernel in ("auto", "site")]
     a, b = pops
     dev = np.abs(b - np.median(b, axis=(1, 2, 3), keepdims=True)).max()
     d = np.abs(a - b)
-    assert d.max() < 8 * 2.0 ** -11 * dev, d.max() / dev
+    assert d.max() < 12 * 2.0 ** -11 * dev, d.max() / dev
     assert (d > 0).any()
-    assert (d > 0).mean() < 0.5
 
 
 @pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
