@@ -488,7 +488,8 @@ def main():
     # end to end through the public API with host buffers: H2D of the initial
     # fields (FP32), flame_init_f32, K steps, flame_moments_f32 and D2H of u,
     # B, J (FP32), and the FP64 scalars.  The context (its state and the CUDA
-    # graph of the first steps) is set up before the timed region.
+    # graph of the first steps) is set up before the timed region, and the
+    # job runs once untimed before the timed run.
     del u_d, B_d
     torch.cuda.empty_cache()
     pin_u = torch.from_numpy(u_h.astype(np.float32)).pin_memory()
@@ -501,31 +502,39 @@ def main():
     outs = {"u": torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev),
             "B": torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev),
             "J": torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev)}
-    barrier()
-    t_wall0 = time.time()
-    t0 = time.perf_counter()
-    marks = [t0]
 
     def mark():  # phase boundaries (a stream synchronisation each; the job's own calls synchronise anyway)
         torch.cuda.synchronize(dev)
         marks.append(time.perf_counter())
 
-    u_d.copy_(pin_u, non_blocking=True)
-    B_d.copy_(pin_B, non_blocking=True)
-    mark()
-    sim.init(None, u_d, B_d)
-    mark()
-    sim.step(args.steps)
-    mark()
-    sim.moments(out=outs)
-    mark()
-    out_h[0:3].copy_(outs["u"], non_blocking=True)
-    out_h[3:6].copy_(outs["B"], non_blocking=True)
-    out_h[6:9].copy_(outs["J"], non_blocking=True)
-    mark()
-    scal = sim.reduce()
-    torch.cuda.synchronize(dev)
-    marks.append(time.perf_counter())
+    def job():
+        u_d.copy_(pin_u, non_blocking=True)
+        B_d.copy_(pin_B, non_blocking=True)
+        mark()
+        sim.init(None, u_d, B_d)
+        mark()
+        sim.step(args.steps)
+        mark()
+        sim.moments(out=outs)
+        mark()
+        out_h[0:3].copy_(outs["u"], non_blocking=True)
+        out_h[3:6].copy_(outs["B"], non_blocking=True)
+        out_h[6:9].copy_(outs["J"], non_blocking=True)
+        mark()
+        r = sim.reduce()
+        torch.cuda.synchronize(dev)
+        marks.append(time.perf_counter())
+        return r
+
+    # one untimed run of the whole job first (the warm-up of the end-to-end
+    # path: first touches of the pinned buffers, the reduction's workspace)
+    marks = [time.perf_counter()]
+    job()
+    barrier()
+    t_wall0 = time.time()
+    t0 = time.perf_counter()
+    marks = [t0]
+    scal = job()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     clocks.window(t_wall0, time.time())
     e2e_sm = clocks.median_in(t_wall0, time.time())

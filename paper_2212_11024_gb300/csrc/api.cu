@@ -474,7 +474,7 @@ flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb)
   if (!c->initialized) return FLAME_ERR_STATE;
   if (nshell < 1 || nshell > 4096) return FLAME_ERR_PARAM;  // shell histogram lives in shared memory
   cudaError_t e;
-  const size_t n3 = (size_t)c->g.n3;
+  const size_t n3 = (size_t)flame::fft_stride(c->g.n3);  // aligned stride between the six fields
   const size_t nc = (size_t)c->g.nz * c->g.ny * (c->g.nx / 2 + 1);
   if (!c->d_fields) {
     e = cudaMalloc(&c->d_fields, 6 * n3 * sizeof(double));
@@ -507,7 +507,8 @@ flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb)
   if (cufftSetStream(c->plan, c->stream) != CUFFT_SUCCESS) return cuda_fail(c, cudaErrorUnknown);
   double* u = c->d_fields;
   double* B = c->d_fields + 3 * n3;
-  e = flame::launch_moments(c->p.storage, c->parity, c->state, c->g, c->k, nullptr, u, B, nullptr, c->stream);
+  e = flame::launch_moments(c->p.storage, c->parity, c->state, c->g, c->k, nullptr, u, B, nullptr, c->stream,
+                            (long long)n3);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_shells, 0, 2 * (size_t)nshell * sizeof(double), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   for (int f = 0; f < 6; ++f) {

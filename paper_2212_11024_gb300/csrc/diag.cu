@@ -201,7 +201,7 @@ struct SiteReal<float> {
 // flame_moments_f32).
 template <class T, bool ODD, class O>
 __global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, O* __restrict__ rho,
-                               O* __restrict__ u, O* __restrict__ B, O* __restrict__ J) {
+                               O* __restrict__ u, O* __restrict__ B, O* __restrict__ J, long long os) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -214,9 +214,9 @@ __global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, 
   const SiteMoments<R> m = site_moments(sf, sg, k);
   if (rho) rho[site] = (O)m.rho(k);
   for (int a = 0; a < 3; ++a) {
-    if (u) u[a * g.n3 + site] = (O)m.U[a];
-    if (B) B[a * g.n3 + site] = (O)m.B(k, a);
-    if (J) J[a * g.n3 + site] = (O)m.J[a];
+    if (u) u[a * os + site] = (O)m.U[a];
+    if (B) B[a * os + site] = (O)m.B(k, a);
+    if (J) J[a * os + site] = (O)m.J[a];
   }
 }
 
@@ -358,12 +358,12 @@ __global__ void reduce_final_kernel(const double* __restrict__ partials, int nbl
 
 template <class T, class O>
 cudaError_t moments_t(int odd, const void* pop, Grid g, const StepConsts& k, O* rho, O* u, O* B, O* J,
-                      cudaStream_t s) {
+                      long long os, cudaStream_t s) {
   const dim3 b = site_block(g), gr = site_grid(g, b);
   if (odd)
-    moments_kernel<T, true, O><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
+    moments_kernel<T, true, O><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J, os);
   else
-    moments_kernel<T, false, O><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J);
+    moments_kernel<T, false, O><<<gr, b, 0, s>>>(static_cast<const T*>(pop), g, k, rho, u, B, J, os);
   return cudaGetLastError();
 }
 
@@ -392,11 +392,12 @@ cudaError_t init_t(int storage, void* pop, Grid g, const StepConsts& k, int none
 
 template <class O>
 cudaError_t moments_any(int storage, int odd, const void* pop, Grid g, const StepConsts& k, O* rho, O* u, O* B,
-                        O* J, cudaStream_t s) {
+                        O* J, long long os, cudaStream_t s) {
+  if (os == 0) os = g.n3;
   switch (storage) {
-    case 1: return moments_t<float, O>(odd, pop, g, k, rho, u, B, J, s);
-    case 2: return moments_t<__half, O>(odd, pop, g, k, rho, u, B, J, s);
-    case 3: return moments_t<__nv_bfloat16, O>(odd, pop, g, k, rho, u, B, J, s);
+    case 1: return moments_t<float, O>(odd, pop, g, k, rho, u, B, J, os, s);
+    case 2: return moments_t<__half, O>(odd, pop, g, k, rho, u, B, J, os, s);
+    case 3: return moments_t<__nv_bfloat16, O>(odd, pop, g, k, rho, u, B, J, os, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -438,13 +439,13 @@ cudaError_t launch_init_f32(int storage, void* pop, Grid g, const StepConsts& k,
 }
 
 cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* rho,
-                           double* u, double* B, double* J, cudaStream_t s) {
-  return moments_any<double>(storage, odd, pop, g, k, rho, u, B, J, s);
+                           double* u, double* B, double* J, cudaStream_t s, long long ostride) {
+  return moments_any<double>(storage, odd, pop, g, k, rho, u, B, J, ostride, s);
 }
 
 cudaError_t launch_moments_f32(int storage, int odd, const void* pop, Grid g, const StepConsts& k, float* rho,
                                float* u, float* B, float* J, cudaStream_t s) {
-  return moments_any<float>(storage, odd, pop, g, k, rho, u, B, J, s);
+  return moments_any<float>(storage, odd, pop, g, k, rho, u, B, J, 0, s);
 }
 
 cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* f,

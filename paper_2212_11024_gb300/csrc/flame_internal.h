@@ -64,8 +64,9 @@ cudaError_t launch_init_f32(int storage, void* pop, Grid g, const StepConsts& k,
                             const float* u, const float* B, const float* gu, const float* gB,
                             unsigned* speed_bits, cudaStream_t s);
 
+// ostride: the stride between the components of u, B and J (0: N3).
 cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* rho,
-                           double* u, double* B, double* J, cudaStream_t s);
+                           double* u, double* B, double* J, cudaStream_t s, long long ostride = 0);
 // The same, written as FP32 (flame_moments_f32).
 cudaError_t launch_moments_f32(int storage, int odd, const void* pop, Grid g, const StepConsts& k, float* rho,
                                float* u, float* B, float* J, cudaStream_t s);
@@ -121,6 +122,12 @@ cudaError_t launch_init_adjoint(Grid g, const StepConsts& k, const double* u, co
 
 cudaError_t launch_shell_bin(const void* spec /* cufftDoubleComplex */, Grid g, int nshell, int zero_mean,
                              double* shells, cudaStream_t s);
+
+// The stride, in elements, between fields handed to cuFFT: N3 rounded up to
+// a multiple of 32, so that every field of an array of fields starts on a
+// 256-byte boundary (cuFFT's transforms need at least the alignment of the
+// complex type, which an odd N3 would break).
+inline long long fft_stride(long long n) { return (n + 31) & ~31LL; }
 
 }  // namespace flame
 

@@ -50,7 +50,9 @@ constexpr int kMaxShell = 1024;  // shell sums of three quantities in shared mem
 
 struct HalfGrid {
   int nx, ny, nz, hx;
-  long long h;  // nz * ny * hx
+  long long h;   // nz * ny * hx modes of a half spectrum
+  long long hp;  // stride between the half spectra of an array (h, 256-byte aligned)
+  long long np;  // stride between the real fields of an array (N3, 256-byte aligned)
 };
 
 HalfGrid half(const Grid& g) {
@@ -60,6 +62,8 @@ HalfGrid half(const Grid& g) {
   q.nz = g.nz;
   q.hx = g.nx / 2 + 1;
   q.h = (long long)g.nz * g.ny * q.hx;
+  q.hp = fft_stride(q.h);
+  q.np = fft_stride(g.n3);
   return q;
 }
 
@@ -102,13 +106,13 @@ __global__ void curl_kernel(const cufftDoubleComplex* __restrict__ F, cufftDoubl
                             HalfGrid q) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < q.h; t += (long long)gridDim.x * blockDim.x) {
     const Mode m = mode_of(t, q);
-    const cufftDoubleComplex a = F[t], b = F[q.h + t], c = F[2 * q.h + t];
+    const cufftDoubleComplex a = F[t], b = F[q.hp + t], c = F[2 * q.hp + t];
     const cufftDoubleComplex x = make_cuDoubleComplex(m.ky * c.x - m.kz * b.x, m.ky * c.y - m.kz * b.y);
     const cufftDoubleComplex y = make_cuDoubleComplex(m.kz * a.x - m.kx * c.x, m.kz * a.y - m.kx * c.y);
     const cufftDoubleComplex z = make_cuDoubleComplex(m.kx * b.x - m.ky * a.x, m.kx * b.y - m.ky * a.y);
     out[t] = times_ik(1.0, x);
-    out[q.h + t] = times_ik(1.0, y);
-    out[2 * q.h + t] = times_ik(1.0, z);
+    out[q.hp + t] = times_ik(1.0, y);
+    out[2 * q.hp + t] = times_ik(1.0, z);
   }
 }
 
@@ -119,33 +123,34 @@ __global__ void grad_kernel(const cufftDoubleComplex* __restrict__ F, cufftDoubl
     const Mode m = mode_of(t, q);
     const cufftDoubleComplex v = F[t];
     out[t] = times_ik(m.kx, v);
-    out[q.h + t] = times_ik(m.ky, v);
-    out[2 * q.h + t] = times_ik(m.kz, v);
+    out[q.hp + t] = times_ik(m.ky, v);
+    out[2 * q.hp + t] = times_ik(m.kz, v);
   }
 }
 
 // nl = inv * sum_a u_a G_a: component b of u . grad u, from the unnormalised
 // inverse transforms G_a of i k_a F(u_b).
+// (fields of an array are np apart)
 __global__ void advect_kernel(const double* __restrict__ u, const double* __restrict__ G, double* __restrict__ nl,
-                              long long n3, double inv) {
+                              long long n3, long long np, double inv) {
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n3; s += (long long)gridDim.x * blockDim.x)
-    nl[s] = inv * (u[s] * G[s] + u[n3 + s] * G[n3 + s] + u[2 * n3 + s] * G[2 * n3 + s]);
+    nl[s] = inv * (u[s] * G[s] + u[np + s] * G[np + s] + u[2 * np + s] * G[2 * np + s]);
 }
 
 // With J the unnormalised inverse transform of F(curl B): N = nl - J x B in
 // place of nl, and W = (u - d_i J) x B in place of J.
 __global__ void flux_fields_kernel(const double* __restrict__ u, const double* __restrict__ B, double* __restrict__ J,
-                                   double* __restrict__ nl, long long n3, double inv, double di) {
+                                   double* __restrict__ nl, long long n3, long long np, double inv, double di) {
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n3; s += (long long)gridDim.x * blockDim.x) {
-    const double b[3] = {B[s], B[n3 + s], B[2 * n3 + s]};
-    const double j[3] = {inv * J[s], inv * J[n3 + s], inv * J[2 * n3 + s]};
-    const double v[3] = {u[s] - di * j[0], u[n3 + s] - di * j[1], u[2 * n3 + s] - di * j[2]};
+    const double b[3] = {B[s], B[np + s], B[2 * np + s]};
+    const double j[3] = {inv * J[s], inv * J[np + s], inv * J[2 * np + s]};
+    const double v[3] = {u[s] - di * j[0], u[np + s] - di * j[1], u[2 * np + s] - di * j[2]};
     nl[s] -= j[1] * b[2] - j[2] * b[1];
-    nl[n3 + s] -= j[2] * b[0] - j[0] * b[2];
-    nl[2 * n3 + s] -= j[0] * b[1] - j[1] * b[0];
+    nl[np + s] -= j[2] * b[0] - j[0] * b[2];
+    nl[2 * np + s] -= j[0] * b[1] - j[1] * b[0];
     J[s] = v[1] * b[2] - v[2] * b[1];
-    J[n3 + s] = v[2] * b[0] - v[0] * b[2];
-    J[2 * n3 + s] = v[0] * b[1] - v[1] * b[0];
+    J[np + s] = v[2] * b[0] - v[0] * b[2];
+    J[2 * np + s] = v[0] * b[1] - v[1] * b[0];
   }
 }
 
@@ -169,7 +174,7 @@ __global__ void budget_bin_kernel(const cufftDoubleComplex* __restrict__ Uh, con
       double tr = 0.0, pu = 0.0, pb = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const cufftDoubleComplex a = Uh[c * q.h + t], x = X[c * q.h + t], b = Bh[c * q.h + t];
+        const cufftDoubleComplex a = Uh[c * q.hp + t], x = X[c * q.hp + t], b = Bh[c * q.hp + t];
         tr += a.x * x.x + a.y * x.y;
         pu += a.x * a.x + a.y * a.y;
         pb += b.x * b.x + b.y * b.y;
@@ -179,12 +184,12 @@ __global__ void budget_bin_kernel(const cufftDoubleComplex* __restrict__ Uh, con
       atomicAdd(&sh[nshell + n], m.w * inv2 * k2 * (nu * pu + eta * pb));
       atomicAdd(&sh[2 * nshell + n], m.w * inv2 * 0.5 * (pu + pb));
     } else {
-      const cufftDoubleComplex a = X[t], b = X[q.h + t], c = X[2 * q.h + t];
+      const cufftDoubleComplex a = X[t], b = X[q.hp + t], c = X[2 * q.hp + t];
       // i k x X
       const cufftDoubleComplex cx = times_ik(1.0, make_cuDoubleComplex(m.ky * c.x - m.kz * b.x, m.ky * c.y - m.kz * b.y));
       const cufftDoubleComplex cy = times_ik(1.0, make_cuDoubleComplex(m.kz * a.x - m.kx * c.x, m.kz * a.y - m.kx * c.y));
       const cufftDoubleComplex cz = times_ik(1.0, make_cuDoubleComplex(m.kx * b.x - m.ky * a.x, m.kx * b.y - m.ky * a.y));
-      const cufftDoubleComplex b0 = Bh[t], b1 = Bh[q.h + t], b2 = Bh[2 * q.h + t];
+      const cufftDoubleComplex b0 = Bh[t], b1 = Bh[q.hp + t], b2 = Bh[2 * q.hp + t];
       const double tr = b0.x * cx.x + b0.y * cx.y + b1.x * cy.x + b1.y * cy.y + b2.x * cz.x + b2.y * cz.y;
       atomicAdd(&sh[n], -m.w * inv2 * tr);
     }
@@ -206,29 +211,31 @@ __global__ void band_kernel(cufftDoubleComplex* __restrict__ Bh, HalfGrid q, int
     if (n >= lo && n <= hi) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const cufftDoubleComplex v = Bh[c * q.h + t];
+        const cufftDoubleComplex v = Bh[c * q.hp + t];
         acc += 0.5 * m.w * inv2 * (v.x * v.x + v.y * v.y);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Bh[c * q.h + t] = make_cuDoubleComplex(0.0, 0.0);
+      for (int c = 0; c < 3; ++c) Bh[c * q.hp + t] = make_cuDoubleComplex(0.0, 0.0);
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(L, acc);
 }
 
-// dL/dB = inv2 * (inverse transform of the masked spectrum), in place; and,
-// when adj is given, the adjoint seed dL/df of the pre-collision populations
-// in natural slot order: 0 for the fluid, dL/dB_b for every D3Q7 velocity of
-// magnetic component b (B_b is the sum of those populations).
-__global__ void band_grad_kernel(double* __restrict__ g, long long n3, double inv2, float* __restrict__ adj) {
+// dL/dB = inv2 * (inverse transform g of the masked spectrum, fields np
+// apart) into dst (fields n3 apart) when given; and, when adj is given, the
+// adjoint seed dL/df of the pre-collision populations in natural slot order:
+// 0 for the fluid, dL/dB_b for every D3Q7 velocity of magnetic component b
+// (B_b is the sum of those populations).
+__global__ void band_grad_kernel(const double* __restrict__ g, long long n3, long long np, double inv2,
+                                 double* __restrict__ dst, float* __restrict__ adj) {
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n3; s += (long long)gridDim.x * blockDim.x) {
     double v[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      v[b] = inv2 * g[b * n3 + s];
-      g[b * n3 + s] = v[b];
+      v[b] = inv2 * g[b * np + s];
+      if (dst) dst[b * n3 + s] = v[b];
     }
     if (adj) {
 #pragma unroll
@@ -260,8 +267,8 @@ cudaError_t ensure_ws(flame_ctx* ctx, const CtxView& v, int nreal, int ncplx, Sp
     w->g = v.g;
     *slot = w;
   }
-  const size_t n3 = (size_t)v.g.n3;
-  const size_t h = (size_t)v.g.nz * v.g.ny * (v.g.nx / 2 + 1);
+  const size_t n3 = (size_t)fft_stride(v.g.n3);
+  const size_t h = (size_t)fft_stride((long long)v.g.nz * v.g.ny * (v.g.nx / 2 + 1));
   cudaError_t e;
   if (w->nreal < nreal) {
     cudaFree(w->real);
@@ -318,6 +325,12 @@ flame_status usable_view(flame_ctx* ctx, CtxView* v, bool fields_given) {
 using flame::CtxView;
 using flame::SpectralWs;
 
+// Copy three caller fields (n3 apart) into workspace fields (np apart).
+static cudaError_t load3(double* dst, const double* src, const flame::HalfGrid& q, long long n3, cudaStream_t st) {
+  return cudaMemcpy2DAsync(dst, q.np * sizeof(double), src, n3 * sizeof(double), n3 * sizeof(double), 3,
+                           cudaMemcpyDeviceToDevice, st);
+}
+
 extern "C" flame_status flame_band_energy(flame_ctx* ctx, int lo, int hi, const double* d_B, double* h_L,
                                           double* d_dLdB, float* d_adj) {
   CtxView v;
@@ -331,22 +344,20 @@ extern "C" flame_status flame_band_energy(flame_ctx* ctx, int lo, int hi, const 
   const flame::HalfGrid q = flame::half(v.g);
   const double inv2 = 1.0 / ((double)n3 * (double)n3);
   double* B = w->real;
-  if (!d_B) {
-    e = flame::launch_moments(v.storage, v.parity, v.state, v.g, v.k, nullptr, nullptr, B, nullptr, v.stream);
-    if (e != cudaSuccess) return flame::fail(ctx, e);
-  }
-  const double* src = d_B ? d_B : B;
-  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, src + c * n3, w->cplx + c * q.h);
+  if (d_B)
+    e = load3(B, d_B, q, n3, v.stream);
+  else
+    e = flame::launch_moments(v.storage, v.parity, v.state, v.g, v.k, nullptr, nullptr, B, nullptr, v.stream, q.np);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, B + c * q.np, w->cplx + c * q.hp);
   double* L = w->hist + 3 * flame::kMaxShell;
   if (e == cudaSuccess) e = cudaMemsetAsync(L, 0, sizeof(double), v.stream);
   if (e != cudaSuccess) return flame::fail(ctx, e);
   flame::band_kernel<<<flame::grid_for(q.h, v.nsm), 256, 0, v.stream>>>(w->cplx, q, lo, hi, inv2, L);
   e = cudaGetLastError();
   if (e == cudaSuccess && (d_dLdB || d_adj)) {
-    double* g = d_dLdB ? d_dLdB : B;
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::z2d(w, w->cplx + c * q.h, g + c * n3);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::z2d(w, w->cplx + c * q.hp, B + c * q.np);
     if (e == cudaSuccess) {
-      flame::band_grad_kernel<<<flame::grid_for(n3, v.nsm), 256, 0, v.stream>>>(g, n3, inv2, d_adj);
+      flame::band_grad_kernel<<<flame::grid_for(n3, v.nsm), 256, 0, v.stream>>>(B, n3, q.np, inv2, d_dLdB, d_adj);
       e = cudaGetLastError();
     }
   }
@@ -362,51 +373,51 @@ extern "C" flame_status flame_energy_budget(flame_ctx* ctx, int nshell, const do
   flame_status st = flame::usable_view(ctx, &v, d_u != nullptr);
   if (st != FLAME_OK) return st;
   if (nshell < 1 || nshell > flame::kMaxShell) return FLAME_ERR_PARAM;
-  // real fields: u, B (when taken from the state), J / W, G (gradient), N;
-  // half spectra: F(u), F(B), and one scratch triple
+  // real fields: u, B, J / W, G (a gradient), N; half spectra: F(u), F(B)
+  // and one scratch triple
   SpectralWs* w = nullptr;
   cudaError_t e = flame::ensure_ws(ctx, v, 15, 9, &w);
   if (e != cudaSuccess) return flame::fail(ctx, e);
   const long long n3 = v.g.n3;
   const flame::HalfGrid q = flame::half(v.g);
+  const long long np = q.np, hp = q.hp;
   const double inv = 1.0 / (double)n3, inv2 = inv * inv;
-  double *U = w->real, *Bf = w->real + 3 * n3, *J = w->real + 6 * n3, *G = w->real + 9 * n3, *NL = w->real + 12 * n3;
-  cufftDoubleComplex *Uh = w->cplx, *Bh = w->cplx + 3 * q.h, *T = w->cplx + 6 * q.h;
-  const double* u = d_u;
-  const double* B = d_B;
-  if (!d_u) {
-    e = flame::launch_moments(v.storage, v.parity, v.state, v.g, v.k, nullptr, U, Bf, nullptr, v.stream);
-    u = U;
-    B = Bf;
+  double *u = w->real, *B = w->real + 3 * np, *J = w->real + 6 * np, *G = w->real + 9 * np, *NL = w->real + 12 * np;
+  cufftDoubleComplex *Uh = w->cplx, *Bh = w->cplx + 3 * hp, *T = w->cplx + 6 * hp;
+  if (d_u) {
+    e = load3(u, d_u, q, n3, v.stream);
+    if (e == cudaSuccess) e = load3(B, d_B, q, n3, v.stream);
+  } else {
+    e = flame::launch_moments(v.storage, v.parity, v.state, v.g, v.k, nullptr, u, B, nullptr, v.stream, np);
   }
   const double nu = (v.tau_nu - 0.5) / 3.0, eta = (v.tau_eta - 0.5) / 4.0;
   const int gh = flame::grid_for(q.h, v.nsm), gr = flame::grid_for(n3, v.nsm);
-  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, u + c * n3, Uh + c * q.h);
-  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, B + c * n3, Bh + c * q.h);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, u + c * np, Uh + c * hp);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, B + c * np, Bh + c * hp);
   if (e != cudaSuccess) return flame::fail(ctx, e);
   // J = curl B (times N3)
   flame::curl_kernel<<<gh, 256, 0, v.stream>>>(Bh, T, q);
   e = cudaGetLastError();
-  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::z2d(w, T + c * q.h, J + c * n3);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::z2d(w, T + c * hp, J + c * np);
   // u . grad u, one component at a time
   for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
-    flame::grad_kernel<<<gh, 256, 0, v.stream>>>(Uh + b * q.h, T, q);
+    flame::grad_kernel<<<gh, 256, 0, v.stream>>>(Uh + b * hp, T, q);
     e = cudaGetLastError();
-    for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = flame::z2d(w, T + a * q.h, G + a * n3);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) e = flame::z2d(w, T + a * hp, G + a * np);
     if (e == cudaSuccess) {
-      flame::advect_kernel<<<gr, 256, 0, v.stream>>>(u, G, NL + b * n3, n3, inv);
+      flame::advect_kernel<<<gr, 256, 0, v.stream>>>(u, G, NL + b * np, n3, np, inv);
       e = cudaGetLastError();
     }
   }
   if (e == cudaSuccess) {
-    flame::flux_fields_kernel<<<gr, 256, 0, v.stream>>>(u, B, J, NL, n3, inv, v.d_i);
+    flame::flux_fields_kernel<<<gr, 256, 0, v.stream>>>(u, B, J, NL, n3, np, inv, v.d_i);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(w->hist, 0, 3 * (size_t)nshell * sizeof(double), v.stream);
   const size_t shm = 3 * (size_t)nshell * sizeof(double);
   for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
     const double* src = pass == 0 ? NL : J;
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, src + c * n3, T + c * q.h);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = flame::d2z(w, src + c * np, T + c * hp);
     if (e == cudaSuccess) {
       flame::budget_bin_kernel<<<gh, 256, shm, v.stream>>>(Uh, Bh, T, q, nshell, pass, nu, eta, inv2, w->hist);
       e = cudaGetLastError();

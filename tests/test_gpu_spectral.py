@@ -118,6 +118,27 @@ def test_band_energy_of_the_state():
     assert abs(L - L0) < 1e-5 * L0
 
 
+@pytest.mark.parametrize("shape", [(9, 7, 11), (5, 6, 7)])
+def test_spectra_on_odd_lattices(shape):
+    """flame_spectra on lattices with an odd site count (fields of its FFTs
+    not 16-byte multiples apart) against the oracle's run."""
+    u, B = turbulence(shape, 47, 0.05, shells=(1, 2))
+    nz, ny, nx = shape
+    sim = _flame(shape, 0.56, 0.6, 1.0)
+    sim.init(None, u, B)
+    sim.step(6)
+    Eu, Eb = sim.spectra(8)
+    sim.close()
+    p = O.Params(nx, ny, nz, 0.56, 0.6, 1.0)
+    pop = O.init(p, None, u, B)
+    O.step(p, pop, 6, literal=False)
+    m = O.moments(p, pop)
+    Eu0 = S.shell_spectrum(m["u"], 8)
+    Eb0 = S.shell_spectrum(m["B"] - m["B"].reshape(3, -1).mean(1)[:, None, None, None], 8)
+    assert np.allclose(Eu, Eu0, rtol=1e-5, atol=1e-6 * Eu0.max())
+    assert np.allclose(Eb, Eb0, rtol=1e-5, atol=1e-6 * Eb0.max())
+
+
 def test_spectral_entry_points_reject_bad_arguments():
     from paper_2212_11024_gb300.flame import FLAME_ERR_PARAM, FLAME_ERR_STATE, library
     lib = library()
