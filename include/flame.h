@@ -26,6 +26,11 @@
  *  - Fields are structure-of-arrays [component][z][y][x], x fastest, with
  *    N3 = nx*ny*nz sites per component.  Gradients are [3a+b][z][y][x] for
  *    d_a F_b.
+ *  - A z-slab context (flame_params.halo_z = 1) of nz planes takes its
+ *    initial fields (flame_init) on nz + 2 planes -- one plane of the
+ *    neighbouring slabs' fields below and above, for the z-derivatives --
+ *    and writes every per-site output (moments, populations, probe,
+ *    reductions) for its own nz planes, N3 = nx*ny*nz sites.
  *
  * Populations are numbered in natural slot order: q = 0..26 the fluid
  * population on App. A's D3Q27 velocity q, q = 27 + 7b + i the magnetic
@@ -105,6 +110,15 @@ typedef struct {
                          one-site kernel; 1: always the one-site kernel.  Both compute
                          the same step in FP32; results agree to FP32 rounding before
                          encoding. */
+    int halo_z;       /* 0: a periodic nx x ny x nz lattice.  1: one z-slab of a larger
+                         periodic lattice split along z (the one-direction domain split
+                         of Sec. 4): the state holds the slab's nz planes between two
+                         ghost planes (nz + 2 planes; plane 0 below, nz + 1 above) that
+                         carry the neighbouring slabs' boundary populations, z is not
+                         wrapped, and the caller exchanges the ghost planes after every
+                         step (flame_halo_exchange, or the runs of flame_halo_plan over
+                         any transport).  Not with FLAME_FD_CURRENT; the spectral and
+                         adjoint entry points refuse slab contexts.                     */
 } flame_params;
 
 typedef struct {
@@ -132,7 +146,8 @@ enum {
 
 typedef struct flame_ctx flame_ctx;
 
-/* Bytes of the population state: 48 * N3 * (4 for FP32, 2 for FP16/BF16).
+/* Bytes of the population state: 48 * N3 * (4 for FP32, 2 for FP16/BF16),
+ * with N3 = nx * ny * (nz + 2 halo_z).
  * graph_steps must be 0 or a positive even number. 
  * Returns 0 for invalid parameters. */
 size_t flame_state_bytes(const flame_params *p);
@@ -211,6 +226,72 @@ flame_status flame_populations(flame_ctx *ctx, double *d_f);
  * cross-helicity, magnetic dissipation, div B estimate).  h_scalars has
  * FLAME_NSCALARS entries (indices FLAME_S_*).  Synchronises. */
 flame_status flame_reduce(flame_ctx *ctx, double *h_scalars);
+
+/* Raw FP64 sums of the scalar diagnostics over the context's sites, for
+ * combining the slabs of a lattice split along z (add the sums of every
+ * slab -- the maximum for FLAME_SUM_UMAX -- and call flame_reduce_combine);
+ * h_sums has FLAME_NSUMS entries.  Synchronises.  Errors as flame_reduce. */
+enum {
+    FLAME_SUM_RHO = 0,       /* sum rho                                */
+    FLAME_SUM_MOMX = 1,      /* sum rho u_x (2: y, 3: z)               */
+    FLAME_SUM_BX = 4,        /* sum B_x (5: y, 6: z)                   */
+    FLAME_SUM_U2 = 7,        /* sum |u|^2                              */
+    FLAME_SUM_DB2 = 8,       /* sum |B - B_ref|^2                      */
+    FLAME_SUM_UDB = 9,       /* sum u . (B - B_ref)                    */
+    FLAME_SUM_UX = 10,       /* sum u_x (11: y, 12: z)                 */
+    FLAME_SUM_J2 = 13,       /* sum |J|^2                              */
+    FLAME_SUM_UMAX = 14,     /* max |u| (combine by maximum)           */
+    FLAME_SUM_DIV2 = 15,     /* sum ((omega_B/C^2) Tr Lambda)^2        */
+    FLAME_SUM_NONFINITE = 16,/* sites with a non-finite moment         */
+    FLAME_SUM_SITES = 17,    /* number of sites summed                 */
+    FLAME_NSUMS = 18
+};
+flame_status flame_reduce_sums(flame_ctx *ctx, double *h_sums);
+
+/* The FLAME_S_* scalars of flame_reduce from raw sums (those of one context,
+ * or the combination of several slabs'), with the reference field B_ref of p.
+ * Host only, no GPU needed.  Returns 0, or -1 for NULL arguments or a zero
+ * site count. */
+int flame_reduce_combine(const flame_params *p, const double *h_sums, double *h_scalars);
+
+/* The halo exchange of a lattice split along z into slab contexts (halo_z =
+ * 1; the paper splits its domain along one direction and exchanges the
+ * boundary nodes every step, Sec. 4).  Under the AA pattern only the odd
+ * step crosses a slab face: it reads, at each face, the populations that
+ * leave the neighbouring slab's boundary plane towards this one (9 fluid
+ * and 3 magnetic storage slots of that plane) and writes back the ones that
+ * leave this slab towards the neighbour.  So after a step that leaves the
+ * state at AA parity 1, every ghost plane receives those slots of the
+ * neighbour's boundary plane; after a step that leaves parity 0, the same
+ * slots of every ghost plane go back into the neighbour's boundary plane.
+ *
+ * flame_halo_plan: the runs of storage slots this slab sends through face
+ * `face` (0: towards z - 1, 1: towards z + 1) and receives there, after a
+ * step that left the state at `parity`: run 0 fluid (9 slots), run 1
+ * magnetic (3 slots).  A run is nslots slot-planes; slot-plane (slot, plane)
+ * is nx*ny contiguous values starting at element (slot * N3s + plane * nx *
+ * ny) of the state, N3s = nx*ny*(nz + 2).  Through a face, this slab's send
+ * run r pairs with the neighbour's receive run r of the opposite face.
+ * Host only.  Returns 0, or -1 for invalid arguments (p not a slab, parity
+ * not 0/1, face not 0/1, NULL outputs). */
+typedef struct {
+    int first_slot;  /* first storage slot of the run                         */
+    int nslots;      /* consecutive storage slots                             */
+    int plane;       /* plane of the state, 0 .. nz + 1 (0 and nz + 1: ghosts) */
+} flame_halo_run;
+int flame_halo_plan(const flame_params *p, int parity, int face, flame_halo_run send[2], flame_halo_run recv[2]);
+
+/* The exchange between two slab contexts on one device (or on devices with
+ * peer access), `upper` being the slab above `lower` (the same context for a
+ * lattice of one slab, whose exchange is its periodic wrap in z): the copies
+ * of flame_halo_plan in both directions through the face between them, as
+ * cudaMemcpy2DAsync on lower's stream.  Call it for every pair of
+ * neighbouring slabs after each step, once all slabs have taken that step;
+ * the work of both contexts must be ordered with that stream (one stream for
+ * all slabs, or events).  Errors: FLAME_ERR_PARAM (not slab contexts, or
+ * nx, ny or storage differ), FLAME_ERR_STATE (not initialised, or at
+ * different step parities), FLAME_ERR_CUDA. */
+flame_status flame_halo_exchange(flame_ctx *lower, flame_ctx *upper);
 
 /* Shell energy spectra of u and B - <B> (Sec. 4.4): with
  * F_hat(m) = N3^-1 sum_x F(x) exp(-2 pi i m.x/N), h_Eu[n] and h_Eb[n] are

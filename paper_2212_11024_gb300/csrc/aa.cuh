@@ -91,6 +91,7 @@ inline dim3 site_block(const Grid& g, int threads = 128) {
   return dim3(bx, by, 1);
 }
 
-inline dim3 site_grid(const Grid& g, dim3 b) { return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz); }
+// One grid z-layer per updated plane (z = blockIdx.z + g.z0).
+inline dim3 site_grid(const Grid& g, dim3 b) { return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nzi); }
 
 }  // namespace flame

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
                         float* __restrict__ lam_out, double* __restrict__ partials) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   const bool live = x < g.nx && y < g.ny;
   double abar_site = 0.0;
   if (live) {
@@ -500,7 +500,7 @@ __global__ void init_adjoint_local_kernel(Grid g, StepConsts k, const double* __
                                           double* __restrict__ partials) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   double abar = 0.0;
   if (x < g.nx && y < g.ny) {
     const long long n3 = g.n3;
@@ -600,7 +600,7 @@ __global__ void init_adjoint_stencil_kernel(Grid g, const double* __restrict__ u
                                             double* __restrict__ ubar, double* __restrict__ Bbar) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   if (x >= g.nx || y >= g.ny) return;
   const long long n3 = g.n3;
   const long long site = ((long long)z * g.ny + y) * g.nx + x;

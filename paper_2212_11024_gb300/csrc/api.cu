@@ -64,9 +64,13 @@ size_t elem_bytes(int storage) { return storage == FLAME_FP32 ? 4 : (storage == 
 flame_status check_params(const flame_params* p) {
   if (!p) return FLAME_ERR_PARAM;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return FLAME_ERR_PARAM;
-  if (p->ny > 65535 || p->nz > 65535) return FLAME_ERR_PARAM;  // grid y / z launch dimensions
-  const long long n3 = (long long)p->nx * p->ny * p->nz;
+  if (p->halo_z != 0 && p->halo_z != 1) return FLAME_ERR_PARAM;
+  if (p->ny > 65535 || p->nz > 65533) return FLAME_ERR_PARAM;  // grid y / z launch dimensions
+  const long long n3 = (long long)p->nx * p->ny * (p->nz + 2 * p->halo_z);
   if (n3 >= (1ll << 31)) return FLAME_ERR_PARAM;
+  // the finite-difference current needs B on the ghost planes, which hold only
+  // the slots a face exchanges
+  if (p->halo_z && p->variant == FLAME_FD_CURRENT) return FLAME_ERR_PARAM;
   if (!(p->tau_nu > 0.5) || !(p->tau_eta > 0.5) || !std::isfinite(p->tau_nu) || !std::isfinite(p->tau_eta))
     return FLAME_ERR_PARAM;
   if (!(p->d_i >= 0.0) || !std::isfinite(p->d_i)) return FLAME_ERR_PARAM;
@@ -113,7 +117,7 @@ flame_status sync_and_check(flame_ctx* c) {
 
 int reduce_blocks(const flame_ctx* c) {
   long long want = (long long)c->nsm * 4;
-  const long long per = (c->g.n3 + 255) / 256;
+  const long long per = (c->g.n3i + 255) / 256;
   if (want > per) want = per;
   if (want < 1) want = 1;
   if (want > flame::kRedBlocksMax) want = flame::kRedBlocksMax;
@@ -190,7 +194,8 @@ static cudaError_t capture_graph(flame_ctx* c, int parity);
 
 size_t flame_state_bytes(const flame_params* p) {
   if (check_params(p) != FLAME_OK) return 0;
-  return (size_t)flame::kPop * (size_t)p->nx * (size_t)p->ny * (size_t)p->nz * elem_bytes(p->storage);
+  return (size_t)flame::kPop * (size_t)p->nx * (size_t)p->ny * (size_t)(p->nz + 2 * p->halo_z) *
+         elem_bytes(p->storage);
 }
 
 flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state, void* stream) {
@@ -230,8 +235,11 @@ flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state,
   for (int a = 0; a < 3; ++a) c->k.Bref[a] = (float)p->B_ref[a];
   c->g.nx = p->nx;
   c->g.ny = p->ny;
-  c->g.nz = p->nz;
-  c->g.n3 = (long long)p->nx * p->ny * p->nz;
+  c->g.nz = p->nz + 2 * p->halo_z;
+  c->g.n3 = (long long)p->nx * p->ny * c->g.nz;
+  c->g.z0 = p->halo_z;
+  c->g.nzi = p->nz;
+  c->g.n3i = (long long)p->nx * p->ny * p->nz;
   // The graph of the first G steps after flame_init (parity 0) is captured
   // here, with the context, so that the first flame_step does not pay for
   // the capture; the parity-1 graph is captured on its first use.
@@ -421,12 +429,12 @@ flame_status flame_probe(flame_ctx* c, int nsites, const long long* d_sites, dou
                                           c->stream));
 }
 
-flame_status flame_reduce(flame_ctx* c, double* h) {
-  const Range range("flame_reduce");
+// The raw FP64 sums of the reduction over the context's sites (FLAME_NSUMS
+// entries: the kRedVals partial sums, then the site count).
+static flame_status reduce_raw(flame_ctx* c, double* r) {
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
-  if (!h) return FLAME_ERR_PARAM;
   cudaError_t e;
   if (!c->d_red) {
     e = cudaMalloc(&c->d_red, sizeof(double) * (size_t)(flame::kRedBlocksMax + 1) * flame::kRedVals);
@@ -439,38 +447,65 @@ flame_status flame_reduce(flame_ctx* c, double* h) {
   double* out = c->d_red + (size_t)flame::kRedBlocksMax * flame::kRedVals;
   e = flame::launch_reduce(c->p.storage, c->parity, c->state, c->g, c->k, nb, c->d_red, out, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
-  double r[flame::kRedVals];
-  e = cudaMemcpyAsync(r, out, sizeof(r), cudaMemcpyDeviceToHost, c->stream);
+  e = cudaMemcpyAsync(r, out, sizeof(double) * flame::kRedVals, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
-  const double n3 = (double)c->g.n3;
+  r[FLAME_SUM_SITES] = (double)c->g.n3i;
+  return FLAME_OK;
+}
+
+static_assert(flame::kRedVals == FLAME_SUM_SITES, "the reduction's partial sums precede the site count");
+
+flame_status flame_reduce_sums(flame_ctx* c, double* h) {
+  const Range range("flame_reduce_sums");
+  if (!h) return FLAME_ERR_PARAM;
+  flame_status st = reduce_raw(c, h);
+  if (st != FLAME_OK) return st;
+  return h[FLAME_SUM_NONFINITE] > 0 ? FLAME_ERR_NONFINITE : FLAME_OK;
+}
+
+int flame_reduce_combine(const flame_params* p, const double* r, double* h) {
+  if (!p || !r || !h || !(r[FLAME_SUM_SITES] > 0)) return -1;
+  const double n3 = r[FLAME_SUM_SITES];
   double Bm[3];
-  h[FLAME_S_MASS] = r[0];
+  h[FLAME_S_MASS] = r[FLAME_SUM_RHO];
   for (int a = 0; a < 3; ++a) {
-    h[FLAME_S_MOMX + a] = r[1 + a];
-    Bm[a] = r[4 + a] / n3;
+    h[FLAME_S_MOMX + a] = r[FLAME_SUM_MOMX + a];
+    Bm[a] = r[FLAME_SUM_BX + a] / n3;
     h[FLAME_S_BX + a] = Bm[a];
   }
-  h[FLAME_S_EU] = 0.5 * r[7] / n3;
+  h[FLAME_S_EU] = 0.5 * r[FLAME_SUM_U2] / n3;
+  // E_B and H_c about the mean field: the sums are taken about B_ref
   double dbm2 = 0.0, hc_corr = 0.0;
   for (int a = 0; a < 3; ++a) {
-    const double d = Bm[a] - c->p.B_ref[a];
+    const double d = Bm[a] - p->B_ref[a];
     dbm2 += d * d;
-    hc_corr += (r[10 + a] / n3) * d;
+    hc_corr += (r[FLAME_SUM_UX + a] / n3) * d;
   }
-  h[FLAME_S_EB] = 0.5 * (r[8] / n3 - dbm2);
-  h[FLAME_S_HC] = r[9] / n3 - hc_corr;
-  h[FLAME_S_J2] = r[13] / n3;
-  h[FLAME_S_UMAX] = r[14];
-  h[FLAME_S_DIVB] = std::sqrt(r[15] / n3);
-  h[FLAME_S_NONFINITE] = r[16];
-  return r[16] > 0 ? FLAME_ERR_NONFINITE : FLAME_OK;
+  h[FLAME_S_EB] = 0.5 * (r[FLAME_SUM_DB2] / n3 - dbm2);
+  h[FLAME_S_HC] = r[FLAME_SUM_UDB] / n3 - hc_corr;
+  h[FLAME_S_J2] = r[FLAME_SUM_J2] / n3;
+  h[FLAME_S_UMAX] = r[FLAME_SUM_UMAX];
+  h[FLAME_S_DIVB] = std::sqrt(r[FLAME_SUM_DIV2] / n3);
+  h[FLAME_S_NONFINITE] = r[FLAME_SUM_NONFINITE];
+  return 0;
+}
+
+flame_status flame_reduce(flame_ctx* c, double* h) {
+  const Range range("flame_reduce");
+  if (!h) return FLAME_ERR_PARAM;
+  double r[FLAME_NSUMS];
+  flame_status st = reduce_raw(c, r);
+  if (st != FLAME_OK) return st;
+  flame_reduce_combine(&c->p, r, h);
+  return r[FLAME_SUM_NONFINITE] > 0 ? FLAME_ERR_NONFINITE : FLAME_OK;
 }
 
 flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb) {
   const Range range("flame_spectra");
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
+  if (c->p.halo_z) return FLAME_ERR_PARAM;  // a slab holds only part of the spectrum's lattice
   if (!c->initialized) return FLAME_ERR_STATE;
   if (nshell < 1 || nshell > 4096) return FLAME_ERR_PARAM;  // shell histogram lives in shared memory
   cudaError_t e;
@@ -565,7 +600,7 @@ flame_status flame_step_adjoint(flame_ctx* c, const void* d_state, int parity, c
                                 float* d_adj_out, double* d_ddi) {
   const Range range("flame_step_adjoint");
   if (!c || !d_state || !d_adj_in || !d_adj_out || !d_ddi) return FLAME_ERR_PARAM;
-  if (c->p.variant != FLAME_SCHEME) return FLAME_ERR_PARAM;
+  if (c->p.variant != FLAME_SCHEME || c->p.halo_z) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
   if (parity != 0 && parity != 1) return FLAME_ERR_STATE;
   if (d_adj_in == d_adj_out) return FLAME_ERR_PARAM;
@@ -585,7 +620,7 @@ flame_status flame_init_adjoint(flame_ctx* c, const double* d_u, const double* d
                                 double* d_ubar, double* d_Bbar, double* d_ddi) {
   const Range range("flame_init_adjoint");
   if (!c || !d_u || !d_B || !d_adj0 || !d_ddi || (!d_ubar && !d_Bbar)) return FLAME_ERR_PARAM;
-  if (c->p.variant != FLAME_SCHEME) return FLAME_ERR_PARAM;
+  if (c->p.variant != FLAME_SCHEME || c->p.halo_z) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
   cudaError_t e;
   if (!c->d_adj_partials) {
@@ -604,6 +639,73 @@ flame_status flame_init_adjoint(flame_ctx* c, const double* d_u, const double* d
   }
   return cuda_fail(c, flame::launch_init_adjoint(c->g, c->k, d_u, d_B, d_adj0, c->d_adj_ws, c->d_adj_partials,
                                                  d_ubar, d_Bbar, d_ddi, c->stream));
+}
+
+int flame_halo_plan(const flame_params* p, int parity, int face, flame_halo_run send[2], flame_halo_run recv[2]) {
+  if (!p || !p->halo_z || p->nz < 1 || (parity != 0 && parity != 1) || (face != 0 && face != 1) || !send || !recv)
+    return -1;
+  // Storage slots of the populations moving down (c_z = -1: fluid slots
+  // 0..8 of the velocity cube, magnetic D3Q7 velocity -z) and up (c_z = +1:
+  // fluid 18..26, magnetic +z).  The face towards z - 1 trades the ones that
+  // cross it: down-movers arrive in the lower ghost plane, up-movers leave
+  // the first plane; through the face towards z + 1 the reverse.
+  const int down_f = 0, up_f = 18, down_m = flame::kQ + 3 * 6, up_m = flame::kQ + 3 * 5;
+  const int lo_ghost = 0, first = 1, last = p->nz, hi_ghost = p->nz + 1;
+  auto set = [](flame_halo_run* r, int f, int m, int plane) {
+    r[0] = flame_halo_run{f, 9, plane};
+    r[1] = flame_halo_run{m, 3, plane};
+  };
+  if (parity == 1) {
+    // before an odd step: ghost planes receive the neighbours' boundary slots
+    if (face == 0) {
+      set(send, up_f, up_m, first);
+      set(recv, down_f, down_m, lo_ghost);
+    } else {
+      set(send, down_f, down_m, last);
+      set(recv, up_f, up_m, hi_ghost);
+    }
+  } else {
+    // after an odd step: what it wrote into the ghost planes goes back
+    if (face == 0) {
+      set(send, down_f, down_m, lo_ghost);
+      set(recv, up_f, up_m, first);
+    } else {
+      set(send, up_f, up_m, hi_ghost);
+      set(recv, down_f, down_m, last);
+    }
+  }
+  return 0;
+}
+
+flame_status flame_halo_exchange(flame_ctx* lo, flame_ctx* up) {
+  const Range range("flame_halo_exchange");
+  if (!lo || !up) return FLAME_ERR_PARAM;
+  if (!lo->p.halo_z || !up->p.halo_z || lo->p.nx != up->p.nx || lo->p.ny != up->p.ny ||
+      lo->p.storage != up->p.storage)
+    return FLAME_ERR_PARAM;
+  if (lo->sticky == FLAME_ERR_CUDA) return lo->sticky;
+  if (up->sticky == FLAME_ERR_CUDA) return up->sticky;
+  if (!lo->initialized || !up->initialized || lo->parity != up->parity) return FLAME_ERR_STATE;
+  const size_t eb = elem_bytes(lo->p.storage);
+  const size_t plane = (size_t)lo->g.nx * lo->g.ny;
+  // through the face between them: lower's face 1 with upper's face 0
+  flame_halo_run ls[2], lr[2], us[2], ur[2];
+  flame_halo_plan(&lo->p, lo->parity, 1, ls, lr);
+  flame_halo_plan(&up->p, up->parity, 0, us, ur);
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+    // lower -> upper, then upper -> lower; one strided copy per run
+    char* ubase = static_cast<char*>(up->state);
+    char* lbase = static_cast<char*>(lo->state);
+    e = cudaMemcpy2DAsync(ubase + ((size_t)ur[r].first_slot * up->g.n3 + ur[r].plane * plane) * eb, up->g.n3 * eb,
+                          lbase + ((size_t)ls[r].first_slot * lo->g.n3 + ls[r].plane * plane) * eb, lo->g.n3 * eb,
+                          plane * eb, ls[r].nslots, cudaMemcpyDeviceToDevice, lo->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(lbase + ((size_t)lr[r].first_slot * lo->g.n3 + lr[r].plane * plane) * eb, lo->g.n3 * eb,
+                            ubase + ((size_t)us[r].first_slot * up->g.n3 + us[r].plane * plane) * eb, up->g.n3 * eb,
+                            plane * eb, us[r].nslots, cudaMemcpyDeviceToDevice, lo->stream);
+  }
+  return cuda_fail(lo, e);
 }
 
 flame_status flame_debug_stall_next_step(flame_ctx* c, unsigned tries) {

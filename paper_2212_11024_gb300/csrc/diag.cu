@@ -37,7 +37,7 @@ __global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq
                             const F* __restrict__ gB, unsigned* __restrict__ speed_bits) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   const bool in = x < g.nx && y < g.ny;
   float sp = 0.f;
   if (in) {
@@ -204,7 +204,7 @@ __global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, 
                                O* __restrict__ u, O* __restrict__ B, O* __restrict__ J, long long os) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   if (x >= g.nx || y >= g.ny) return;
   const int site = (z * g.ny + y) * g.nx + x;
   const Nbr nb = make_nbr(x, y, z, g);
@@ -212,11 +212,12 @@ __global__ void moments_kernel(const T* __restrict__ pop, Grid g, StepConsts k, 
   R sf[kQ], sg[3][kM];
   load_site<T, ODD>(pop, site, nb, g.n3, sf, sg);
   const SiteMoments<R> m = site_moments(sf, sg, k);
-  if (rho) rho[site] = (O)m.rho(k);
+  const long long o = site - (long long)g.z0 * g.nx * g.ny;  // index among the updated sites
+  if (rho) rho[o] = (O)m.rho(k);
   for (int a = 0; a < 3; ++a) {
-    if (u) u[a * os + site] = (O)m.U[a];
-    if (B) B[a * os + site] = (O)m.B(k, a);
-    if (J) J[a * os + site] = (O)m.J[a];
+    if (u) u[a * os + o] = (O)m.U[a];
+    if (B) B[a * os + o] = (O)m.B(k, a);
+    if (J) J[a * os + o] = (O)m.J[a];
   }
 }
 
@@ -224,7 +225,7 @@ template <class T, bool ODD>
 __global__ void populations_kernel(const T* __restrict__ pop, Grid g, StepConsts k, double* __restrict__ f) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   if (x >= g.nx || y >= g.ny) return;
   const int site = (z * g.ny + y) * g.nx + x;
   const Nbr nb = make_nbr(x, y, z, g);
@@ -232,15 +233,16 @@ __global__ void populations_kernel(const T* __restrict__ pop, Grid g, StepConsts
   load_site<T, ODD, double>(pop, site, nb, g.n3, sf, sg);
   const double Br[3] = {(double)k.Bref[0], (double)k.Bref[1], (double)k.Bref[2]};
   const double br2 = Br[0] * Br[0] + Br[1] * Br[1] + Br[2] * Br[2];
+  const long long o = site - (long long)g.z0 * g.nx * g.ny;  // index among the updated sites
 #pragma unroll 1
   for (int i = 0; i < kQ; ++i) {
     const double c2 = cx27(i) * cx27(i) + cy27(i) * cy27(i) + cz27(i) * cz27(i);
     const double cb = cx27(i) * Br[0] + cy27(i) * Br[1] + cz27(i) * Br[2];
     const double ell = 4.5 * (0.5 * br2 * (c2 - 1.0 / 3.0) - cb * cb);  // rest Lorentz term / w
-    f[(long long)i * g.n3 + site] = w27d(i) * ((double)k.rho0 + ell + sf[i]);
+    f[(long long)i * g.n3i + o] = w27d(i) * ((double)k.rho0 + ell + sf[i]);
   }
   for (int b = 0; b < 3; ++b)
-    for (int i = 0; i < kM; ++i) f[(long long)mslot(b, i) * g.n3 + site] = w7d(i) * (Br[b] + sg[b][i]);
+    for (int i = 0; i < kM; ++i) f[(long long)mslot(b, i) * g.n3i + o] = w7d(i) * (Br[b] + sg[b][i]);
 }
 
 
@@ -251,11 +253,11 @@ __global__ void probe_kernel(const T* __restrict__ pop, Grid g, StepConsts k, in
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const long long sl = sites[j];
-  if (sl < 0 || sl >= g.n3) {
+  if (sl < 0 || sl >= g.n3i) {
     for (int v = 0; v < 10; ++v) out[(long long)j * 10 + v] = nan("");
     return;
   }
-  const int site = (int)sl;
+  const int site = (int)(sl + (long long)g.z0 * g.nx * g.ny);
   const int x = site % g.nx, y = (site / g.nx) % g.ny, z = site / (g.nx * g.ny);
   const Nbr nb = make_nbr(x, y, z, g);
   using R = typename SiteReal<T>::type;
@@ -294,8 +296,9 @@ __global__ void reduce_kernel(const T* __restrict__ pop, Grid g, StepConsts k, d
 #pragma unroll
   for (int v = 0; v < kRedVals; ++v) acc[v] = 0.0;
   const long long n3 = g.n3;
-  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n3; s += (long long)gridDim.x * blockDim.x) {
-    const int site = (int)s;
+  const long long off = (long long)g.z0 * g.nx * g.ny;
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.n3i; s += (long long)gridDim.x * blockDim.x) {
+    const int site = (int)(s + off);
     const int x = site % g.nx, y = (site / g.nx) % g.ny, z = site / (g.nx * g.ny);
     const Nbr nb = make_nbr(x, y, z, g);
     using R = typename SiteReal<T>::type;
@@ -393,7 +396,7 @@ cudaError_t init_t(int storage, void* pop, Grid g, const StepConsts& k, int none
 template <class O>
 cudaError_t moments_any(int storage, int odd, const void* pop, Grid g, const StepConsts& k, O* rho, O* u, O* B,
                         O* J, long long os, cudaStream_t s) {
-  if (os == 0) os = g.n3;
+  if (os == 0) os = g.n3i;
   switch (storage) {
     case 1: return moments_t<float, O>(odd, pop, g, k, rho, u, B, J, os, s);
     case 2: return moments_t<__half, O>(odd, pop, g, k, rho, u, B, J, os, s);

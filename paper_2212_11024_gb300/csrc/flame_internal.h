@@ -16,9 +16,16 @@ struct StepConsts {
   float Bref[3];  // reference field of the deviation encoding
 };
 
+// The lattice a context updates.  A periodic lattice updates all its nz
+// planes (z0 = 0, nzi = nz).  A z-slab of a larger lattice (flame_params
+// .halo_z) holds its nzi planes between two ghost planes, nz = nzi + 2, and
+// updates planes z0 = 1 .. nzi; its ghost planes hold the neighbouring
+// slabs' boundary slots, exchanged between steps.
 struct Grid {
-  int nx, ny, nz;
-  long long n3;
+  int nx, ny, nz;  // planes held in the state
+  long long n3;    // nx * ny * nz: the stride between storage slots
+  int z0, nzi;     // the planes updated: z0 .. z0 + nzi - 1
+  long long n3i;   // nx * ny * nzi: the sites updated, and the size of per-site outputs
 };
 
 // Scheme variants (flame_variant).

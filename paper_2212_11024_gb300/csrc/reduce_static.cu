@@ -100,7 +100,7 @@ extern "C" flame_status flame_reduce_static(flame_ctx* ctx, int nblocks, double*
   if (nblocks < 0 || nblocks > FLAME_STATIC_REDUCE_BLOCKS_MAX) return FLAME_ERR_PARAM;
   if (nblocks == 0) {
     long long want = (long long)v.nsm * 4;
-    const long long per = (v.g.n3 + 255) / 256;
+    const long long per = (v.g.n3i + 255) / 256;
     if (want > per) want = per;
     if (want > FLAME_STATIC_REDUCE_BLOCKS_MAX) want = FLAME_STATIC_REDUCE_BLOCKS_MAX;
     nblocks = want < 1 ? 1 : (int)want;
@@ -111,7 +111,7 @@ extern "C" flame_status flame_reduce_static(flame_ctx* ctx, int nblocks, double*
   if (e != cudaSuccess) return static_cast<flame_status>(flame_ctx_cuda_fail(ctx, e));
   e = flame::launch_reduce_partials(v.storage, v.parity, v.state, v.g, v.k, nblocks, scratch, v.stream);
   if (e != cudaSuccess) return static_cast<flame_status>(flame_ctx_cuda_fail(ctx, e));
-  finalize_kernel<<<1, 32, 0, v.stream>>>(scratch, nblocks, (double)v.g.n3, v.Bref[0], v.Bref[1], v.Bref[2],
+  finalize_kernel<<<1, 32, 0, v.stream>>>(scratch, nblocks, (double)v.g.n3i, v.Bref[0], v.Bref[1], v.Bref[2],
                                           d_scalars);
   return static_cast<flame_status>(flame_ctx_cuda_fail(ctx, cudaGetLastError()));
 }

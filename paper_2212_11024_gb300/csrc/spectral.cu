@@ -315,6 +315,7 @@ flame_status fail(flame_ctx* ctx, cudaError_t e) { return static_cast<flame_stat
 flame_status usable_view(flame_ctx* ctx, CtxView* v, bool fields_given) {
   if (flame_ctx_view(ctx, v) != 0) return FLAME_ERR_PARAM;
   if (v->status != FLAME_OK && v->status != FLAME_ERR_NONFINITE) return static_cast<flame_status>(v->status);
+  if (v->g.z0 != 0) return FLAME_ERR_PARAM;  // a z-slab holds only part of the lattice the spectra need
   if (!fields_given && !v->initialized) return FLAME_ERR_STATE;
   return FLAME_OK;
 }

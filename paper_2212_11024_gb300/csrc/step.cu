@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
     step_kernel(Slots<T> P, Grid g, StepConsts k, unsigned* __restrict__ flag, const float* __restrict__ Bfd) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   if (x >= g.nx || y >= g.ny) return;
   const int site = (z * g.ny + y) * g.nx + x;
   const Nbr nb = make_nbr(x, y, z, g);
@@ -277,7 +277,7 @@ template <class T, bool ODD>
 __global__ void bfield_kernel(Slots<T> P, Grid g, float* __restrict__ Bfd) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + g.z0;
   if (x >= g.nx || y >= g.ny) return;
   const int site = (z * g.ny + y) * g.nx + x;
   const Nbr nb = make_nbr(x, y, z, g);

@@ -532,14 +532,14 @@ struct RowIO {
   T* rows;  // [stage][48 storage slots][nx]
   unsigned long long* bars;
   long long n3;
-  int nx, ny, nz;
+  int nx, ny, nz, z0;  // tile t is the row (y, z) = (t % ny, t / ny + z0)
   unsigned rowbytes;
   int lane;
   bool boxed, stall;
   const RowMaps* maps;
 
   __device__ __forceinline__ void issue(int tile, int st) const {
-    const int y = tile % ny, z = tile / ny;
+    const int y = tile % ny, z = tile / ny + z0;
     const unsigned bar = smem_addr(&bars[st]);
     T* dst = rows + (size_t)st * kPop * nx;
     if (lane == 0) mbar_expect_tx(bar, kPop * rowbytes);
@@ -565,7 +565,7 @@ struct RowIO {
   // (DEFER: the refill waits for it itself, later).
   template <int STAGES, bool DEFER>
   __device__ __forceinline__ void store(int tile, int st) const {
-    const int y = tile % ny, z = tile / ny;
+    const int y = tile % ny, z = tile / ny + z0;
     const T* src = rows + (size_t)st * kPop * nx;
     if (boxed) {
       if (!ODD) {
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
   const unsigned rowbytes = static_cast<unsigned>(nx) * sizeof(T);
   T* rows = reinterpret_cast<T*>(smem);  // [stage][48 storage slots][nx]
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kRowStages * kPop * rowbytes);
-  const int ntiles = ny * nz;
+  const int ntiles = ny * g.nzi;  // rows of the updated planes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool boxed = nx <= kBoxMaxX;
 
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
   }
   __syncthreads();
 
-  const RowIO<T, ODD> io{state, rows, bars, g.n3, nx, ny, nz, rowbytes, lane, boxed, wt.stall != 0, &maps};
+  const RowIO<T, ODD> io{state, rows, bars, g.n3, nx, ny, nz, g.z0, rowbytes, lane, boxed, wt.stall != 0, &maps};
 
   const int first = blockIdx.x, stride = gridDim.x;
   // Tiles staged before the loop: both stages with two; with three, two of
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
       auto ldg = [&](int c, int i) { return A.ld(kQ + 3 * (ODD ? opp7(i) : i) + c, -mx7(i)); };
       PairGlobal<T, ODD> G;
       if constexpr (kDirect) {
-        const int y = tile % ny, z = tile / ny;
+        const int y = tile % ny, z = tile / ny + g.z0;
         G.state = state;
         G.n3 = g.n3;
         G.x0 = A.x0;
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
       // J = periodic central-difference curl of the pre-collision field at
       // the pair (the face neighbours in y and z are whole-pair loads).
       auto curl_b = [&](f2 (&J)[3]) {
-        const int y = tile % ny, z = tile / ny;
+        const int y = tile % ny, z = tile / ny + g.z0;
         const long long r0 = ((long long)z * ny + y) * nx;
         const long long ryp = ((long long)z * ny + wrap(y + 1, ny)) * nx;
         const long long rym = ((long long)z * ny + wrap(y - 1, ny)) * nx;
@@ -794,7 +794,7 @@ cudaError_t row_config(const Grid& g, int* grid, size_t* smem_out) {
     c.occ_smem = smem;
   }
   if (c.nsm == 0 && (e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const long long ntiles = (long long)g.ny * g.nz, slots = (long long)c.occ * c.nsm;
+  const long long ntiles = (long long)g.ny * g.nzi, slots = (long long)c.occ * c.nsm;
   *grid = (int)(ntiles < slots ? ntiles : slots);
   *smem_out = smem;
   return cudaSuccess;

@@ -51,7 +51,12 @@ class Params(ctypes.Structure):
         ("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("B_ref", ctypes.c_double * 3),
         ("init_noneq", ctypes.c_int), ("check_every", ctypes.c_int), ("strict_cfl", ctypes.c_int),
         ("graph_steps", ctypes.c_int), ("variant", ctypes.c_int), ("kernel", ctypes.c_int),
+        ("halo_z", ctypes.c_int),
     ]
+
+
+class HaloRun(ctypes.Structure):
+    _fields_ = [("first_slot", ctypes.c_int), ("nslots", ctypes.c_int), ("plane", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -97,6 +102,10 @@ def _lib():
             "flame_moments_f32": (i, [vp, vp, vp, vp, vp]),
             "flame_band_energy": (i, [vp, i, i, vp, P(d), vp, vp]),
             "flame_energy_budget": (i, [vp, i, vp, vp, P(d), P(d), P(d)]),
+            "flame_reduce_sums": (i, [vp, P(d)]),
+            "flame_reduce_combine": (i, [P(Params), P(d), P(d)]),
+            "flame_halo_plan": (i, [P(Params), i, i, P(HaloRun), P(HaloRun)]),
+            "flame_halo_exchange": (i, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -121,7 +130,7 @@ def lattice():
 
 def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
                 init_noneq=True, check_every=0, strict_cfl=False, graph_steps=0, variant="flame",
-                kernel="auto") -> Params:
+                kernel="auto", halo_z=False) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.tau_nu, p.tau_eta, p.d_i = float(tau_nu), float(tau_eta), float(d_i)
@@ -133,7 +142,31 @@ def make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_re
     p.graph_steps = int(graph_steps)
     p.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
     p.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
+    p.halo_z = int(bool(halo_z))
     return p
+
+
+NSUMS = 18
+SUM_UMAX = 14
+
+
+def reduce_combine(p: Params, sums) -> dict:
+    """flame_reduce_combine: the reduce() scalars from raw sums (one
+    context's, or several slabs' added, with the maximum at SUM_UMAX)."""
+    r = (ctypes.c_double * NSUMS)(*[float(v) for v in sums])
+    h = (ctypes.c_double * NSCALARS)()
+    if _lib().flame_reduce_combine(ctypes.byref(p), r, h) != 0:
+        raise ValueError("flame_reduce_combine: invalid sums")
+    return dict(zip(SCALAR_NAMES, list(h)))
+
+
+def halo_plan(p: Params, parity: int, face: int):
+    """flame_halo_plan: ([(first_slot, nslots, plane)] * 2 sent, the same
+    received) through `face` of a slab after a step leaving `parity`."""
+    send, recv = (HaloRun * 2)(), (HaloRun * 2)()
+    if _lib().flame_halo_plan(ctypes.byref(p), int(parity), int(face), send, recv) != 0:
+        raise ValueError("flame_halo_plan: invalid arguments")
+    return ([(r.first_slot, r.nslots, r.plane) for r in send], [(r.first_slot, r.nslots, r.plane) for r in recv])
 
 
 def state_bytes(p: Params) -> int:
@@ -175,7 +208,7 @@ class Flame:
 
     def __init__(self, nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
                  init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None, graph_steps=0,
-                 variant="flame", kernel="auto"):
+                 variant="flame", kernel="auto", halo_z=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -184,8 +217,10 @@ class Flame:
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.p = make_params(nx, ny, nz, tau_nu, tau_eta, d_i, storage, rho0, B_ref, init_noneq, check_every,
-                             strict_cfl, graph_steps, variant, kernel)
+                             strict_cfl, graph_steps, variant, kernel, halo_z)
         self.shape = (int(nz), int(ny), int(nx))
+        # a z-slab takes its initial fields with one neighbouring plane on each side
+        self.field_shape = (int(nz) + 2 * int(bool(halo_z)), int(ny), int(nx))
         self.n3 = int(nx) * int(ny) * int(nz)
         nbytes = state_bytes(self.p)
         if nbytes == 0:
@@ -210,7 +245,7 @@ class Flame:
         if isinstance(a, np.ndarray):
             a = t.from_numpy(np.ascontiguousarray(a))
         a = a.to(device=self.device, dtype=dtype).contiguous()
-        want = (ncomp,) + self.shape if ncomp else self.shape
+        want = (ncomp,) + self.field_shape if ncomp else self.field_shape
         if tuple(a.shape) != want:
             raise ValueError(f"expected shape {want}, got {tuple(a.shape)}")
         return a
@@ -329,6 +364,21 @@ class Flame:
             _check(rc, "flame_reduce")
         vals["status"] = rc
         return vals
+
+    def reduce_sums(self):
+        """flame_reduce_sums: the raw FP64 sums (NSUMS values, numpy) behind
+        reduce(), to be added over the slabs of a lattice and combined with
+        reduce_combine."""
+        h = (ctypes.c_double * NSUMS)()
+        rc = self._lib.flame_reduce_sums(self._ctx_or_raise(), h)
+        if rc not in (FLAME_OK, FLAME_ERR_NONFINITE):
+            _check(rc, "flame_reduce_sums")
+        return np.array(h[:])
+
+    def halo_exchange(self, upper):
+        """flame_halo_exchange with the slab context `upper` above this one
+        (this context itself for a lattice of one slab)."""
+        _check(self._lib.flame_halo_exchange(self._ctx_or_raise(), upper._ctx_or_raise()), "flame_halo_exchange")
 
     def reduce_static(self, nblocks=0, out=None):
         """flame_reduce_static: the reduce() scalars computed without any
