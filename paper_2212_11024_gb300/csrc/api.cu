@@ -46,7 +46,7 @@ struct flame_ctx {
   int nshell_cap;
   cufftHandle plan;
   bool has_plan;
-  float* d_bfield;           // 3 N3 floats, FLAME_FD_CURRENT only
+  void* d_bfield;            // [3][N3] values of the storage type, FLAME_FD_CURRENT only
   cudaGraphExec_t graph[2];  // graph_steps launches starting at parity 0 / 1
   bool has_graph[2];
   double* d_adj_partials;  // adjoint_partials_needed doubles
@@ -223,7 +223,7 @@ flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state,
     return FLAME_ERR_CUDA;
   }
   if (p->variant == FLAME_FD_CURRENT &&
-      cudaMalloc(&c->d_bfield, 3 * sizeof(float) * (size_t)p->nx * p->ny * p->nz) != cudaSuccess) {
+      cudaMalloc(&c->d_bfield, 3 * elem_bytes(p->storage) * (size_t)p->nx * p->ny * p->nz) != cudaSuccess) {
     cudaFree(c->d_flags);
     delete c;
     return FLAME_ERR_CUDA;

@@ -34,12 +34,13 @@ constexpr int kVarBgkFluid = 1;   // BGK fluid collision
 constexpr int kVarEmhd = 2;       // electron MHD magnetic equilibrium
 constexpr int kVarFdCurrent = 3;  // J from the central-difference curl of B
 
-// storage: 1 FP32, 2 FP16, 3 BF16 (flame_storage).  Bfd: 3 N3 floats of
-// scratch, required by kVarFdCurrent only.
+// storage: 1 FP32, 2 FP16, 3 BF16 (flame_storage).  Bfd: scratch for the
+// pre-collision B - B_ref, [3][N3] values of the storage's element type,
+// required by kVarFdCurrent only.
 // kernel: 0 the row kernel where step_row_supported, else the one-site
 // kernel; 1 always the one-site kernel.
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                        cudaStream_t s, int variant = kVarFlame, float* Bfd = nullptr, int kernel = 0);
+                        cudaStream_t s, int variant = kVarFlame, void* Bfd = nullptr, int kernel = 0);
 
 // The step for 16-bit storage as a persistent kernel over x rows staged in
 // shared memory by TMA, two sites per thread in packed FP32 pairs
@@ -51,16 +52,16 @@ bool step_row_supported(Grid g, int storage, int variant, const void* pop);
 // Settles the launch configuration of the kernel launch_step would use
 // (no launch); needed once before stream capture.
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel);
-// Bfd: the pre-collision B - B_ref (3 N3 floats) that launch_bfield wrote,
+// Bfd: the pre-collision B - B_ref ([3][N3], storage type) that launch_bfield wrote,
 // read by kVarFdCurrent only.  stall_tries > 0: the failure-path test -- the
 // launch arms its barriers without issuing copies and gives up after
 // stall_tries polls per wait.
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                            cudaStream_t s, int variant = kVarFlame, const float* Bfd = nullptr,
+                            cudaStream_t s, int variant = kVarFlame, const void* Bfd = nullptr,
                             unsigned stall_tries = 0);
 // The pre-pass of kVarFdCurrent: B - B_ref of the pre-collision populations
-// at every site into Bfd (FP32, [3][N3]).
-cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, float* Bfd, cudaStream_t s);
+// at every site into Bfd ([3][N3] in the storage's element type).
+cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, void* Bfd, cudaStream_t s);
 
 cudaError_t launch_init(int storage, void* pop, Grid g, const StepConsts& k, int noneq, const double* rho,
                         const double* u, const double* B, const double* gu, const double* gB,

@@ -42,10 +42,10 @@ constexpr int kStepMinBlocks = 3;
 
 // VAR selects the scheme: kVarFlame (the paper's), kVarBgkFluid, kVarEmhd or
 // kVarFdCurrent (flame_internal.h); Bfd is the pre-collision B - B_ref field
-// written by bfield_kernel, read only by kVarFdCurrent.
+// (storage type) written by the B pre-pass, read only by kVarFdCurrent.
 template <class T, bool ODD, int VAR>
 __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
-    step_kernel(Slots<T> P, Grid g, StepConsts k, unsigned* __restrict__ flag, const float* __restrict__ Bfd) {
+    step_kernel(Slots<T> P, Grid g, StepConsts k, unsigned* __restrict__ flag, const T* __restrict__ Bfd) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z + g.z0;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
   if constexpr (VAR == kVarFdCurrent) {
     // J = periodic central-difference curl of the pre-collision field
     const long long n3 = g.n3;
-    auto Bn = [&](int b, int off) { return Bfd[b * n3 + site + off]; };
+    auto Bn = [&](int b, int off) { return Codec<T>::dec(Bfd[b * n3 + site + off]); };
     const float J[3] = {0.5f * ((Bn(2, nb.yp) - Bn(2, nb.ym)) - (Bn(1, nb.zp) - Bn(1, nb.zm))),
                         0.5f * ((Bn(0, nb.zp) - Bn(0, nb.zm)) - (Bn(2, nb.xp) - Bn(2, nb.xm))),
                         0.5f * ((Bn(1, nb.xp) - Bn(1, nb.xm)) - (Bn(0, nb.yp) - Bn(0, nb.ym)))};
@@ -271,10 +271,10 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks)
 }
 
 
-// B - B_ref of the pre-collision populations at every site (FP32), for the
-// finite-difference current variant.
+// B - B_ref of the pre-collision populations at every site, in the storage's
+// element type, for the finite-difference current variant.
 template <class T, bool ODD>
-__global__ void bfield_kernel(Slots<T> P, Grid g, float* __restrict__ Bfd) {
+__global__ void bfield_kernel(Slots<T> P, Grid g, T* __restrict__ Bfd) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z + g.z0;
@@ -288,14 +288,65 @@ __global__ void bfield_kernel(Slots<T> P, Grid g, float* __restrict__ Bfd) {
     for (int i = 0; i < kM; ++i)
       v += (i == 0 ? 0.25f : 0.125f) *
            Codec<T>::dec(P.p[mslot(b, ODD ? opp7(i) : i)][site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i))]);
-    Bfd[(long long)b * g.n3 + site] = v;
+    Bfd[(long long)b * g.n3 + site] = Codec<T>::enc(v);
+  }
+}
+
+// The same for 16-bit storage and even nx, two sites (x0, x0 + 1), x0 even,
+// per thread: the pair of a slot whose source is not shifted along x is one
+// 32-bit load, the x-shifted sources (D3Q7 +-x on odd steps) two 16-bit
+// loads, and the pair of B values one 32-bit store.  The sums run in the
+// order of bfield_kernel, so both give the same B.
+template <class T, bool ODD>
+__global__ void bfield2_kernel(Slots<T> P, Grid g, T* __restrict__ Bfd) {
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z + g.z0;
+  if (x0 >= g.nx || y >= g.ny) return;
+  const int s0 = (z * g.ny + y) * g.nx + x0;
+  const Nbr n0 = make_nbr(x0, y, z, g), n1 = make_nbr(x0 + 1, y, z, g);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < kM; ++i) {
+      const T* p = P.p[mslot(b, ODD ? opp7(i) : i)];
+      const float w = i == 0 ? 0.25f : 0.125f;
+      float a, c;
+      if (!ODD || mx7(i) == 0) {
+        // y and z offsets only: the same for both sites, and even
+        const float2 v = dec2(p + s0 + src_off<ODD>(n0, 0, my7(i), mz7(i)));
+        a = v.x;
+        c = v.y;
+      } else {
+        a = Codec<T>::dec(p[s0 + src_off<ODD>(n0, mx7(i), 0, 0)]);
+        c = Codec<T>::dec(p[s0 + 1 + src_off<ODD>(n1, mx7(i), 0, 0)]);
+      }
+      v0 += w * a;
+      v1 += w * c;
+    }
+    enc2(Bfd + (long long)b * g.n3 + s0, v0, v1);
   }
 }
 
 template <class T>
-cudaError_t bfield_t(int odd, const void* pop, Grid g, float* Bfd, cudaStream_t s) {
-  const dim3 bb = site_block(g, 128), gb = site_grid(g, bb);
+cudaError_t bfield_t(int odd, const void* pop, Grid g, void* Bfd_, cudaStream_t s) {
+  T* Bfd = static_cast<T*>(Bfd_);
   const Slots<T> P = make_slots<T>(pop, g);
+  if constexpr (sizeof(T) == 2) {
+    if (g.nx % 2 == 0) {
+      const int pairs = g.nx / 2;
+      const int bx = pairs >= 128 ? 128 : ((pairs + 31) / 32) * 32;
+      const int by = 128 / bx < g.ny ? 128 / bx : g.ny;
+      const dim3 bb(bx, by, 1), gb((pairs + bx - 1) / bx, (g.ny + by - 1) / by, g.nzi);
+      if (odd)
+        bfield2_kernel<T, true><<<gb, bb, 0, s>>>(P, g, Bfd);
+      else
+        bfield2_kernel<T, false><<<gb, bb, 0, s>>>(P, g, Bfd);
+      return cudaGetLastError();
+    }
+  }
+  const dim3 bb = site_block(g, 128), gb = site_grid(g, bb);
   if (odd)
     bfield_kernel<T, true><<<gb, bb, 0, s>>>(P, g, Bfd);
   else
@@ -304,7 +355,7 @@ cudaError_t bfield_t(int odd, const void* pop, Grid g, float* Bfd, cudaStream_t 
 }
 
 template <class T, int VAR>
-void step_launch(int odd, const Slots<T>& P, Grid g, const StepConsts& k, unsigned* flag, const float* Bfd, dim3 gr,
+void step_launch(int odd, const Slots<T>& P, Grid g, const StepConsts& k, unsigned* flag, const T* Bfd, dim3 gr,
                  dim3 b, cudaStream_t s) {
   if (odd)
     step_kernel<T, true, VAR><<<gr, b, 0, s>>>(P, g, k, flag, Bfd);
@@ -313,7 +364,7 @@ void step_launch(int odd, const Slots<T>& P, Grid g, const StepConsts& k, unsign
 }
 
 template <class T>
-cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, int variant, float* Bfd,
+cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag, int variant, void* Bfd,
                    cudaStream_t s) {
   const dim3 b = site_block(g, kStepThreads), gr = site_grid(g, b);
   const Slots<T> P = make_slots<T>(pop, g);
@@ -325,7 +376,7 @@ cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fl
       if (!Bfd) return cudaErrorInvalidValue;
       const cudaError_t e = bfield_t<T>(odd, pop, g, Bfd, s);
       if (e != cudaSuccess) return e;
-      step_launch<T, kVarFdCurrent>(odd, P, g, k, flag, Bfd, gr, b, s);
+      step_launch<T, kVarFdCurrent>(odd, P, g, k, flag, static_cast<const T*>(Bfd), gr, b, s);
       break;
     }
     default: return cudaErrorInvalidValue;
@@ -336,7 +387,7 @@ cudaError_t step_t(int odd, void* pop, Grid g, const StepConsts& k, unsigned* fl
 
 }  // namespace
 
-cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, float* Bfd, cudaStream_t s) {
+cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, void* Bfd, cudaStream_t s) {
   if (!Bfd) return cudaErrorInvalidValue;
   switch (storage) {
     case 1: return bfield_t<float>(odd, pop, g, Bfd, s);
@@ -347,7 +398,7 @@ cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, float* 
 }
 
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                        cudaStream_t s, int variant, float* Bfd, int kernel) {
+                        cudaStream_t s, int variant, void* Bfd, int kernel) {
   if (kernel == 0 && step_row_supported(g, storage, variant, pop)) {
     if (variant == kVarFdCurrent) {
       const cudaError_t e = launch_bfield(storage, odd, pop, g, Bfd, s);

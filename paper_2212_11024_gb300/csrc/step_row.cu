@@ -75,7 +75,7 @@ cudaError_t row_variant(int variant, const RowCall& c) {
 }  // namespace
 
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                            cudaStream_t s, int variant, const float* Bfd, unsigned stall_tries) {
+                            cudaStream_t s, int variant, const void* Bfd, unsigned stall_tries) {
   const RowWait wt{stall_tries ? stall_tries : kWaitTries, stall_tries ? 1 : 0};
   return row_variant(variant, RowCall{storage, odd, pop, g, k, flag, Bfd, s, true, wt});
 }
@@ -83,7 +83,7 @@ cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepC
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel) {
   if (kernel != 0 || !step_row_supported(g, storage, variant, pop)) return cudaSuccess;
   // a placeholder field: only the configuration is settled, nothing is read
-  static const float no_field = 0.f;
+  static const unsigned no_field = 0u;
   for (int odd = 0; odd < 2; ++odd) {
     const cudaError_t e = row_variant(variant, RowCall{storage, odd, const_cast<void*>(pop), g, StepConsts{}, nullptr,
                                                        &no_field, nullptr, false, RowWait{kWaitTries, 0}});

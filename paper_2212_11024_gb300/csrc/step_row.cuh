@@ -63,7 +63,7 @@ struct RowWait {
 };
 
 // One step of the row kernel: storage 2 FP16 / 3 BF16, AA parity odd; Bfd
-// the pre-collision B - B_ref (3 N3 floats) for the finite-difference
+// the pre-collision B - B_ref ([3][N3], storage type) for the finite-difference
 // current, else unused; launch false only settles the launch configuration.
 struct RowCall {
   int storage, odd;
@@ -71,7 +71,7 @@ struct RowCall {
   Grid g;
   StepConsts k;
   unsigned* flag;
-  const float* Bfd;
+  const void* Bfd;
   cudaStream_t s;
   bool launch;
   RowWait wt;
@@ -598,11 +598,11 @@ struct RowIO {
 constexpr int row_bound_threads(int nx) { return nx ? nx / 2 : kRowMaxThreads; }
 constexpr int row_bound_blocks(int nx) { return 512 / row_bound_threads(nx); }
 
-// Bfd: the pre-collision B - B_ref ([3][N3] floats), read by kVarFdCurrent only.
+// Bfd: the pre-collision B - B_ref ([3][N3], storage type), read by kVarFdCurrent only.
 template <class T, bool ODD, int NX, int kRowStages, int VAR>
 __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
     step_row_kernel(T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
-                    const float* __restrict__ Bfd, const __grid_constant__ RowMaps maps, RowWait wt) {
+                    const T* __restrict__ Bfd, const __grid_constant__ RowMaps maps, RowWait wt) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nx = NX ? NX : g.nx, ny = g.ny, nz = g.nz;
   const unsigned rowbytes = static_cast<unsigned>(nx) * sizeof(T);
@@ -694,12 +694,14 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
         const long long rym = ((long long)z * ny + wrap(y - 1, ny)) * nx;
         const long long rzp = ((long long)wrap(z + 1, nz) * ny + y) * nx;
         const long long rzm = ((long long)wrap(z - 1, nz) * ny + y) * nx;
-        const float *Bx = Bfd, *By = Bfd + g.n3, *Bz = Bfd + 2 * g.n3;
-        auto at = [&](const float* b, long long r) { return f2{__ldg(reinterpret_cast<const float2*>(b + r + A.x0))}; };
+        const T *Bx = Bfd, *By = Bfd + g.n3, *Bz = Bfd + 2 * g.n3;
+        // the pair (x0, x1) of a row as one 32-bit load, a single value as one 16-bit load
+        auto at = [&](const T* b, long long r) { return f2{dec2(b + r + A.x0)}; };
+        auto one = [&](const T* b, long long i) { return Codec<T>::dec(b[i]); };
         const f2 by0 = at(By, r0), bz0 = at(Bz, r0);
         // B(x + 1) - B(x - 1) at x = x0, x1
-        const f2 dxBy = pack(by0.v.y, __ldg(By + r0 + A.xp1)) - pack(__ldg(By + r0 + A.xm0), by0.v.x);
-        const f2 dxBz = pack(bz0.v.y, __ldg(Bz + r0 + A.xp1)) - pack(__ldg(Bz + r0 + A.xm0), bz0.v.x);
+        const f2 dxBy = pack(by0.v.y, one(By, r0 + A.xp1)) - pack(one(By, r0 + A.xm0), by0.v.x);
+        const f2 dxBz = pack(bz0.v.y, one(Bz, r0 + A.xp1)) - pack(one(Bz, r0 + A.xm0), bz0.v.x);
         J[0] = 0.5f * ((at(Bz, ryp) - at(Bz, rym)) - (at(By, rzp) - at(By, rzm)));
         J[1] = 0.5f * ((at(Bx, rzp) - at(Bx, rzm)) - dxBz);
         J[2] = 0.5f * (dxBy - (at(Bx, ryp) - at(Bx, rym)));
@@ -809,7 +811,8 @@ cudaError_t row_launch(const RowCall& c) {
   if (e == cudaSuccess && c.g.nx <= kBoxMaxX) e = row_maps(c.pop, c.g, &maps);
   if (e != cudaSuccess || !c.launch) return e;
   step_row_kernel<T, ODD, NX, S, VAR>
-      <<<grid, c.g.nx / 2, smem, c.s>>>(static_cast<T*>(c.pop), c.g, c.k, c.flag, c.Bfd, maps, c.wt);
+      <<<grid, c.g.nx / 2, smem, c.s>>>(static_cast<T*>(c.pop), c.g, c.k, c.flag, static_cast<const T*>(c.Bfd),
+                                        maps, c.wt);
   return cudaGetLastError();
 }
 
