@@ -49,6 +49,27 @@ def test_maxima_and_metric_definitions():
     assert abs(eps_nu) < 1e-9
 
 
+def test_zmode_metrics():
+    """The z-mode's amplitude at the origin: exact on the exact series (the
+    A-mode removed by (A/C) u_z); a series running 1 % slow gives
+    eps_phi_z = -0.01; a z-mode decaying 5 % faster gives eps_r_z = 0.05
+    while the x- and y-modes decay as before."""
+    s = V.lattice_setup(32, 0.01, 1e-3)
+    t = np.linspace(0, 4 * s["period"], 4001)
+    ue = V.exact_origin(t, s)
+    a = V.zmode(ue, s)
+    dec = np.exp(-s["nu_lbm"] * s["k"] ** 2 * t)
+    assert np.allclose(np.abs(a), np.abs(a[0]) * dec, rtol=1e-12)
+    assert np.allclose(V.zmode_errors(t, ue, s), 0.0, atol=1e-12)
+    assert abs(V.zmode_errors(t, V.exact_origin(t / 1.01, s), s)[0] + 0.01) < 1e-9
+    faster = ue.copy()
+    extra = np.exp(-0.05 * s["nu_lbm"] * s["k"] ** 2 * t)
+    faster[:, 0] = (ue[:, 0] - s["U0"] * V.A_AMP * dec) * extra + s["U0"] * V.A_AMP * dec
+    faster[:, 1] = ue[:, 1] * extra
+    eps_phi_z, eps_r_z = V.zmode_errors(t, faster, s)
+    assert abs(eps_phi_z) < 1e-9 and abs(eps_r_z - 0.05) < 1e-9
+
+
 def test_oracle_follows_exact_origin_series():
     """FP64 oracle, N = 16, one fifth of a period (Ma = 0.05, nu = 7e-3, so
     tau_nu ~ 0.51 and the modes decay by ~e^-1.4): u(0, t) within 10 % of the
