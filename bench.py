@@ -309,6 +309,48 @@ def oracle_restriction_errors(storages, dev):
 
 
 # --------------------------------------------------------------------------- replicas (N > 1)
+# The decaying-turbulence runs of the paper's Sec. 5 setting that the
+# benchmark records besides its headline (each from seeded random-phase
+# solenoidal fields in shells 1..4, flat E(k), rho = 1, tau = 0.51):
+# 128^3 FP32 storage, rms 0.05, d_i in {0, 0.05 * 128}, 1000 steps; and
+# 512^3 FP16 storage, rms 0.04, d_i in {0, 0.02, 0.05, 0.1} * 512, 2000 steps.
+TURBULENCE_RUNS = (
+    dict(n=128, storage="fp32", rms=0.05, d_i=(0.0, 6.4), steps=1000, seeds=(1, 2)),
+    dict(n=512, storage="fp16", rms=0.04, d_i=(0.0, 10.24, 25.6, 51.2), steps=2000, seeds=(1, 2)),
+)
+
+
+def turbulence_runs(dev, every=100):
+    """Each run of TURBULENCE_RUNS: steps completed, where it went non-finite,
+    step-kernel GLUPS (CUDA events around the step chunks only), the energy
+    ratio E(end)/E(0) and the slope of E_B(k) over k = 8..32 at the end."""
+    import numpy as np
+    import torch
+
+    from paper_2212_11024_gb300 import inputs, turbulence
+
+    out = []
+    for cfg in TURBULENCE_RUNS:
+        n = cfg["n"]
+        u, B = inputs.turbulence((n, n, n), *cfg["seeds"], cfg["rms"], cfg["rms"], shells=(1, 4))
+        fields = (u.astype(np.float32), B.astype(np.float32))
+        del u, B
+        for di in cfg["d_i"]:
+            r = turbulence.decay(n, di, cfg["steps"], spectra_every=every, storage=cfg["storage"], rms_u=cfg["rms"],
+                                 rms_b=cfg["rms"], seeds=cfg["seeds"], graph_steps=20, device=dev, fields=fields)
+            E = [s["E_u"] + s["E_B"] for s in r["scalars"]]
+            k = np.arange(8, 33)
+            eb = r["Eb"][-1][8:33]
+            slope = float(np.polyfit(np.log(k), np.log(eb), 1)[0]) if np.all(eb > 0) else None
+            out.append(dict(n=n, storage=cfg["storage"], rms=cfg["rms"], d_i=di, steps=cfg["steps"],
+                            steps_done=int(r["steps"]), first_nonfinite=r["first_nonfinite"],
+                            glups=r["mlups"] / 1e3, E_end_over_E0=float(E[-1] / E[0]),
+                            Eb_slope_k8_32=slope, spectra_every=every))
+        del fields
+        torch.cuda.empty_cache()
+    return out
+
+
 def reduce_max(x, dist=None, device=None):
     """The largest x over the ranks of the default process group (x itself
     without one): every rank gets the slowest rank's time."""
@@ -340,6 +382,8 @@ def main():
     ap.add_argument("--impl", default="flame", choices=["flame", "reference"])
     ap.add_argument("--storage", default="fp16,fp32,bf16,fp16/site,bf16/site",
                     help="first entry is the headline; '/site' forces the one-site kernel")
+    ap.add_argument("--no-turbulence-runs", action="store_true",
+                    help="skip the 128^3 and 512^3 decaying-turbulence runs recorded besides the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the host-oracle legs (CPU baseline and the 64^3 oracle accuracy check)")
     args = ap.parse_args()
@@ -507,6 +551,8 @@ def main():
         torch.cuda.synchronize(dev)
         marks.append(time.perf_counter())
 
+    copy_stream = torch.cuda.Stream(dev)
+
     def job():
         u_d.copy_(pin_u, non_blocking=True)
         B_d.copy_(pin_B, non_blocking=True)
@@ -516,12 +562,17 @@ def main():
         sim.step(args.steps)
         mark()
         sim.moments(out=outs)
-        mark()
-        out_h[0:3].copy_(outs["u"], non_blocking=True)
-        out_h[3:6].copy_(outs["B"], non_blocking=True)
-        out_h[6:9].copy_(outs["J"], non_blocking=True)
-        mark()
+        # the fields go to the host on a copy stream while the library's
+        # stream computes the FP64 scalars from the state
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ready)
+            out_h[0:3].copy_(outs["u"], non_blocking=True)
+            out_h[3:6].copy_(outs["B"], non_blocking=True)
+            out_h[6:9].copy_(outs["J"], non_blocking=True)
         r = sim.reduce()
+        copy_stream.synchronize()
         torch.cuda.synchronize(dev)
         marks.append(time.perf_counter())
         return r
@@ -548,9 +599,13 @@ def main():
                   "pinned host (FP32), flame_reduce scalars", "seconds": e2e_s, "gpu_launches": 1 + args.steps + 1 + 2,
            "final_E_u": scal["E_u"], "final_E_B": scal["E_B"],
            "phases_ms": {k: (marks[i + 1] - marks[i]) * 1e3 for i, k in
-                         enumerate(("h2d", "init", "steps", "moments", "d2h", "reduce"))},
+                         enumerate(("h2d", "init", "steps", "moments + d2h overlapped with reduce"))},
            "sm_mhz": e2e_sm}
     clk = clocks.stop()
+
+    turb = None
+    if world == 1 and not args.no_turbulence_runs:
+        turb = turbulence_runs(dev)
 
     # The host-oracle legs come last: their OpenMP threads keep the host cores
     # busy for a while after they finish, which would slow the host side of
@@ -598,7 +653,7 @@ def main():
                      "kernel_source_sha256_16": kernel_source_hash()},
         "stated_l2_error": accuracy.get(head, {}).get("vs_oracle_64"),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
-        "variants": variants, "adjoint_step": adjoint, "accuracy": accuracy,
+        "variants": variants, "adjoint_step": adjoint, "accuracy": accuracy, "turbulence_runs": turb,
     }
     print(json.dumps(line), flush=True)
 

@@ -10,11 +10,14 @@ namespace {
 // ---------------------------------------------------------------------------
 // Initialisation (once per run).  The arithmetic type R is FP64 for FP32
 // storage and FP32 for 16-bit storage, whose encoding rounds to 2^-11 (FP16)
-// or 2^-8 (BF16) relative, far above FP32's 2^-24; gradients are taken in
-// FP64 from the FP64 fields either way.
+// or 2^-8 (BF16) relative, far above FP32's 2^-24; the gradients too are
+// taken in R.
 
-template <class F>
-__device__ __forceinline__ double cdiff(const F* f, int a, int x, int y, int z, const Grid& g) {
+// Periodic central difference of field f along axis a at (x, y, z), in the
+// per-site arithmetic type R (GB300's FP64 pipe is 1/64 of its FP32 rate, so
+// 16-bit storage, whose values keep 11 or 8 bits, takes them in FP32).
+template <class R, class F>
+__device__ __forceinline__ R cdiff(const F* f, int a, int x, int y, int z, const Grid& g) {
   int xp = x, xm = x, yp = y, ym = y, zp = z, zm = z;
   if (a == 0) {
     xp = x + 1 == g.nx ? 0 : x + 1;
@@ -26,7 +29,7 @@ __device__ __forceinline__ double cdiff(const F* f, int a, int x, int y, int z, 
     zp = z + 1 == g.nz ? 0 : z + 1;
     zm = z == 0 ? g.nz - 1 : z - 1;
   }
-  return 0.5 * ((double)f[((long long)zp * g.ny + yp) * g.nx + xp] - (double)f[((long long)zm * g.ny + ym) * g.nx + xm]);
+  return (R)0.5 * ((R)f[((long long)zp * g.ny + yp) * g.nx + xp] - (R)f[((long long)zm * g.ny + ym) * g.nx + xm]);
 }
 
 // F: the element type of the caller's fields (FP64 for flame_init, FP32 for
@@ -51,8 +54,8 @@ __global__ void init_kernel(T* __restrict__ pop, Grid g, StepConsts k, int noneq
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        du[3 * a + b] = (R)(gu ? gu[(3 * a + b) * n3 + site] : cdiff(u + b * n3, a, x, y, z, g));
-        dB[3 * a + b] = (R)(gB ? gB[(3 * a + b) * n3 + site] : cdiff(Bf + b * n3, a, x, y, z, g));
+        du[3 * a + b] = gu ? (R)gu[(3 * a + b) * n3 + site] : cdiff<R>(u + b * n3, a, x, y, z, g);
+        dB[3 * a + b] = gB ? (R)gB[(3 * a + b) * n3 + site] : cdiff<R>(Bf + b * n3, a, x, y, z, g);
       }
     const R J0[3] = {dB[5] - dB[7], dB[6] - dB[2], dB[1] - dB[3]};  // curl B
     const R omega = (R)k.omega, omegaB = (R)k.omegaB, aH = (R)k.alphaH;
