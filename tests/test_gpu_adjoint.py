@@ -114,7 +114,7 @@ def test_checkpointed_gradient_matches_fp64_autograd():
     pop = R.step(R.init(ut, Bt, tau_nu, tau_eta, dt), tau_nu, tau_eta, dt, n)
     Lr = R.band_energy(R.magnetic_field(pop), 1, 2)
     gu, gB, gd = torch.autograd.grad(Lr, [ut, Bt, dt])
-    assert abs(float(L.detach()) - float(Lr)) < 1e-5 * float(Lr)
+    assert abs(float(L.detach()) - float(Lr.detach())) < 1e-5 * float(Lr.detach())
 
     def rel(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
