@@ -105,11 +105,14 @@ typedef struct {
     int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant), nx a
                          multiple of 64 in 64..1024 other than 576 and 640 (the row
                          lengths where it was timed faster) and a 16-byte aligned state
-                         use the row kernel (x rows staged in shared memory by TMA, two
-                         sites per thread in packed FP32 pairs), everything else the
-                         one-site kernel; 1: always the one-site kernel.  Both compute
-                         the same step in FP32; results agree to FP32 rounding before
-                         encoding. */
+                         use the row kernel (x rows staged in shared memory, two sites
+                         per thread in packed FP32 pairs), everything else the one-site
+                         kernel; 1: always the one-site kernel; 2: the row kernel with a
+                         whole row per block tile, 3: with half a row per tile (rows of
+                         more than 256 sites), where the row kernel applies, else the
+                         one-site kernel.  All compute the same step in FP32; results
+                         agree to FP32 rounding before encoding (the row kernel's tilings
+                         agree bit for bit). */
     int halo_z;       /* 0: a periodic nx x ny x nz lattice.  1: one z-slab of a larger
                          periodic lattice split along z (the one-direction domain split
                          of Sec. 4): the state holds the slab's nz planes between two

@@ -81,7 +81,7 @@ flame_status check_params(const flame_params* p) {
   if (p->check_every < 0) return FLAME_ERR_PARAM;
   if (p->graph_steps < 0 || (p->graph_steps & 1)) return FLAME_ERR_PARAM;
   if (p->variant < FLAME_SCHEME || p->variant > FLAME_FD_CURRENT) return FLAME_ERR_PARAM;
-  if (p->kernel < 0 || p->kernel > 1) return FLAME_ERR_PARAM;
+  if (p->kernel < 0 || p->kernel > 3) return FLAME_ERR_PARAM;
   return FLAME_OK;
 }
 
@@ -340,7 +340,7 @@ flame_status flame_step(flame_ctx* c, int n) {
     // The wait-failure test: one launch whose waits all run out; it leaves
     // the state as it was, so step and parity do not advance.
     cudaError_t e = flame::launch_step_row(c->p.storage, c->parity, c->state, c->g, c->k, c->d_flags, c->stream,
-                                           c->p.variant, c->d_bfield, c->stall_tries);
+                                           c->p.variant, c->d_bfield, c->stall_tries, c->p.kernel);
     c->stall_tries = 0;
     if (e != cudaSuccess) return cuda_fail(c, e);
     return sync_and_check(c);
@@ -712,7 +712,7 @@ flame_status flame_debug_stall_next_step(flame_ctx* c, unsigned tries) {
   flame_status st = usable(c);
   if (st != FLAME_OK) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
-  if (tries == 0 || c->p.kernel != 0 || !flame::step_row_supported(c->g, c->p.storage, c->p.variant, c->state))
+  if (tries == 0 || !flame::step_row_supported(c->g, c->p.storage, c->p.variant, c->state, c->p.kernel))
     return FLAME_ERR_PARAM;
   c->stall_tries = tries;
   return FLAME_OK;

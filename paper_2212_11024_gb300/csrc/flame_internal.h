@@ -37,28 +37,31 @@ constexpr int kVarFdCurrent = 3;  // J from the central-difference curl of B
 // storage: 1 FP32, 2 FP16, 3 BF16 (flame_storage).  Bfd: scratch for the
 // pre-collision B - B_ref, [3][N3] values of the storage's element type,
 // required by kVarFdCurrent only.
-// kernel: 0 the row kernel where step_row_supported, else the one-site
-// kernel; 1 always the one-site kernel.
+// kernel (flame_params.kernel): 0 the row kernel where step_row_supported
+// (whole rows or half rows as row_auto_segments chooses), else the one-site
+// kernel; 1 always the one-site kernel; 2 the row kernel on whole rows and
+// 3 on half rows, where they apply (else the one-site kernel).
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
                         cudaStream_t s, int variant = kVarFlame, void* Bfd = nullptr, int kernel = 0);
 
 // The step for 16-bit storage as a persistent kernel over x rows staged in
-// shared memory by TMA, two sites per thread in packed FP32 pairs
-// (step_row.cuh): every variant, 64 <= nx <= 1024 with nx a multiple of 64
-// where the row kernel is the faster one (all but 576 and 640), a
-// 16-byte aligned state.  flag bit 1: a non-finite moment; bit 2: a staged
-// copy did not complete within the wait limit.
-bool step_row_supported(Grid g, int storage, int variant, const void* pop);
+// shared memory (step_row.cuh), two sites per thread in packed FP32 pairs:
+// every variant, 64 <= nx <= 1024 with nx a multiple of 64 (automatic
+// choice: where the row kernel is the faster one, all but 576 and 640), a
+// 16-byte aligned state; half rows for nx > 256 only.  flag bit 1: a
+// non-finite moment; bit 2: a staged copy did not complete within the wait
+// limit.
+bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel = 0);
 // Settles the launch configuration of the kernel launch_step would use
 // (no launch); needed once before stream capture.
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel);
 // Bfd: the pre-collision B - B_ref ([3][N3], storage type) that launch_bfield wrote,
 // read by kVarFdCurrent only.  stall_tries > 0: the failure-path test -- the
 // launch arms its barriers without issuing copies and gives up after
-// stall_tries polls per wait.
+// stall_tries polls per wait.  kernel as for launch_step (0, 2 or 3).
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
                             cudaStream_t s, int variant = kVarFlame, const void* Bfd = nullptr,
-                            unsigned stall_tries = 0);
+                            unsigned stall_tries = 0, int kernel = 0);
 // The pre-pass of kVarFdCurrent: B - B_ref of the pre-collision populations
 // at every site into Bfd ([3][N3] in the storage's element type).
 cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, void* Bfd, cudaStream_t s);

@@ -399,12 +399,12 @@ cudaError_t launch_bfield(int storage, int odd, const void* pop, Grid g, void* B
 
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
                         cudaStream_t s, int variant, void* Bfd, int kernel) {
-  if (kernel == 0 && step_row_supported(g, storage, variant, pop)) {
+  if (step_row_supported(g, storage, variant, pop, kernel)) {
     if (variant == kVarFdCurrent) {
       const cudaError_t e = launch_bfield(storage, odd, pop, g, Bfd, s);
       if (e != cudaSuccess) return e;
     }
-    return launch_step_row(storage, odd, pop, g, k, flag, s, variant, Bfd);
+    return launch_step_row(storage, odd, pop, g, k, flag, s, variant, Bfd, 0, kernel);
   }
   switch (storage) {
     case 1: return step_t<float>(odd, pop, g, k, flag, variant, Bfd, s);

@@ -56,11 +56,21 @@ cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 // warps.
 bool row_kernel_wins(int nx) { return nx != 576 && nx != 640; }
 
-bool step_row_supported(Grid g, int storage, int variant, const void* pop) {
-  return variant >= kVarFlame && variant <= kVarFdCurrent && (storage == 2 || storage == 3) && g.nx >= 64 &&
-         g.nx <= 2 * kRowMaxThreads && g.nx % 64 == 0 && row_kernel_wins(g.nx) &&
-         (reinterpret_cast<uintptr_t>(pop) & 15u) == 0;
+// Segments per tile of the automatic choice (kernel = 0).
+int row_auto_segments(int nx) { return nx > 256 ? 1 : 1; }
+
+bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel) {
+  if (kernel == 1) return false;
+  const bool base = variant >= kVarFlame && variant <= kVarFdCurrent && (storage == 2 || storage == 3) &&
+                    g.nx >= 64 && g.nx <= 2 * kRowMaxThreads && g.nx % 64 == 0 &&
+                    (reinterpret_cast<uintptr_t>(pop) & 15u) == 0;
+  if (!base) return false;
+  if (kernel == 3) return g.nx > kBoxMaxX;  // half rows: rows of more than 256 sites
+  if (kernel == 2) return true;
+  return row_kernel_wins(g.nx);
 }
+
+int row_segments(int nx, int kernel) { return kernel == 3 ? 2 : kernel == 2 ? 1 : row_auto_segments(nx); }
 
 namespace {
 cudaError_t row_variant(int variant, const RowCall& c) {
@@ -75,18 +85,19 @@ cudaError_t row_variant(int variant, const RowCall& c) {
 }  // namespace
 
 cudaError_t launch_step_row(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
-                            cudaStream_t s, int variant, const void* Bfd, unsigned stall_tries) {
+                            cudaStream_t s, int variant, const void* Bfd, unsigned stall_tries, int kernel) {
   const RowWait wt{stall_tries ? stall_tries : kWaitTries, stall_tries ? 1 : 0};
-  return row_variant(variant, RowCall{storage, odd, pop, g, k, flag, Bfd, s, true, wt});
+  return row_variant(variant, RowCall{storage, odd, row_segments(g.nx, kernel), pop, g, k, flag, Bfd, s, true, wt});
 }
 
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel) {
-  if (kernel != 0 || !step_row_supported(g, storage, variant, pop)) return cudaSuccess;
+  if (!step_row_supported(g, storage, variant, pop, kernel)) return cudaSuccess;
   // a placeholder field: only the configuration is settled, nothing is read
   static const unsigned no_field = 0u;
   for (int odd = 0; odd < 2; ++odd) {
-    const cudaError_t e = row_variant(variant, RowCall{storage, odd, const_cast<void*>(pop), g, StepConsts{}, nullptr,
-                                                       &no_field, nullptr, false, RowWait{kWaitTries, 0}});
+    const cudaError_t e = row_variant(variant, RowCall{storage, odd, row_segments(g.nx, kernel), const_cast<void*>(pop),
+                                                       g, StepConsts{}, nullptr, &no_field, nullptr, false,
+                                                       RowWait{kWaitTries, 0}});
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

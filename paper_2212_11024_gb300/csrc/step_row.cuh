@@ -27,7 +27,8 @@
 // The scheme variants are instantiations of the same kernel (template
 // parameter VAR): the BGK fluid collision (Sec. 3.1.1), the electron-MHD
 // magnetic equilibrium (Sec. 5) and the current from the central-difference
-// curl of B (read from the FP32 field that step.cu's pre-pass writes).  Each
+// curl of B (read from the field that step.cu's pre-pass writes in the
+// storage's type).  Each
 // variant is instantiated in a translation unit of its own (step_row.cu,
 // step_row_bgk.cu, step_row_emhd.cu, step_row_fd.cu), so they compile in
 // parallel.
@@ -67,6 +68,7 @@ struct RowWait {
 // current, else unused; launch false only settles the launch configuration.
 struct RowCall {
   int storage, odd;
+  int segments;  // 1: a tile is a whole row; 2: half a row (rows of more than 256 sites)
   void* pop;
   Grid g;
   StepConsts k;
@@ -459,20 +461,38 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// A row split into H segments (H = 2 for long rows: a tile is half a row,
+// so a block needs half the threads and half the shared memory) stages each
+// segment with kHalo values of its neighbours on each side, so that the odd
+// step's x shift stays inside the staged copy; kHalo 16-bit values are one
+// 16-byte unit, the granule of the bulk copies.
+constexpr int kHalo = 8;
+
+// Width of a staged row: the row itself, or a segment with its halos.
+__host__ __device__ constexpr int staged_width(int nx, int H) { return H == 1 ? nx : nx / H + 2 * kHalo; }
+
 // The site pair (2t, 2t + 1) of a staged tile: ld(s, d) reads staged
 // storage slot s at the pair moved by d sites (d = -c_x reads velocity c on
 // an odd step; d = 0 on even steps), st(s, d, v) writes it there.  NX > 0
 // fixes the row length at compile time (shared-memory offsets become
-// immediates); NX = 0 reads it from the grid.
-template <class T, bool ODD, int NX>
+// immediates); NX = 0 reads it from the grid.  Whole rows (H = 1) wrap the
+// shift around the row; a segment (H > 1) reads its halo.
+template <class T, bool ODD, int NX, int H = 1>
 struct PairAccess {
   const T* R;
-  int nx, x0, x1, xm0, xp1;
-  __device__ __forceinline__ PairAccess(const T* rows, int n) : R(rows), nx(NX ? NX : n) {
-    x0 = 2 * threadIdx.x;
-    x1 = x0 + 1;
-    xm0 = x0 == 0 ? nx - 1 : x0 - 1;
-    xp1 = x1 == nx - 1 ? 0 : x1 + 1;
+  int nx, x0, x1, xm0, xp1;  // nx: the staged row width
+  __device__ __forceinline__ PairAccess(const T* rows, int n) : R(rows), nx(staged_width(NX ? NX : n, H)) {
+    if constexpr (H == 1) {
+      x0 = 2 * threadIdx.x;
+      x1 = x0 + 1;
+      xm0 = x0 == 0 ? nx - 1 : x0 - 1;
+      xp1 = x1 == nx - 1 ? 0 : x1 + 1;
+    } else {
+      x0 = kHalo + 2 * threadIdx.x;
+      x1 = x0 + 1;
+      xm0 = x0 - 1;
+      xp1 = x1 + 1;
+    }
   }
   __device__ __forceinline__ f2 ld(int s, int d) const {
     const T* r = R + s * nx;
@@ -525,20 +545,28 @@ struct PairGlobal {
 // Warp 0 moves the 48 rows of tile (y, z) between HBM and stage st: the rows
 // (y, z) of all storage slots on even steps, run r of three storage slots
 // from the row (y, z) + (run_dy(r), run_dz(r)) on odd steps.  The store
-// writes each row back to where it was loaded from.
-template <class T, bool ODD>
+// writes each row back to where it was loaded from.  With H = 2 segments a
+// tile is the segment h = tile % 2 of row tile / 2 (sites h W .. h W + W - 1,
+// W = nx / 2), staged with bulk copies at offset kHalo of a row of
+// staged_width(nx, 2) values: on odd steps with its halos, the one at the
+// row's end (periodic) by a copy of its own; its results are stored directly.
+template <class T, bool ODD, int H = 1>
 struct RowIO {
   T* state;
-  T* rows;  // [stage][48 storage slots][nx]
+  T* rows;  // [stage][48 storage slots][staged_width(nx, H)]
   unsigned long long* bars;
   long long n3;
-  int nx, ny, nz, z0;  // tile t is the row (y, z) = (t % ny, t / ny + z0)
-  unsigned rowbytes;
+  int nx, ny, nz, z0;  // tile t is the row (y, z) = (r % ny, r / ny + z0), r = t / H
+  unsigned rowbytes;   // bytes of a whole row
   int lane;
   bool boxed, stall;
   const RowMaps* maps;
 
   __device__ __forceinline__ void issue(int tile, int st) const {
+    if constexpr (H > 1) {
+      issue_segment(tile, st);
+      return;
+    }
     const int y = tile % ny, z = tile / ny + z0;
     const unsigned bar = smem_addr(&bars[st]);
     T* dst = rows + (size_t)st * kPop * nx;
@@ -557,6 +585,43 @@ struct RowIO {
         const int r = s / 3;
         const int ys = ODD ? wrap(y + run_dy(r), ny) : y, zs = ODD ? wrap(z + run_dz(r), nz) : z;
         bulk_load(smem_addr(dst + s * nx), state + (size_t)s * n3 + ((long long)zs * ny + ys) * nx, rowbytes, bar);
+      }
+    }
+  }
+
+  // Half-row segments (H = 2): every staged row of the segment, by bulk
+  // copies of whole 16-byte units (W and kHalo are multiples of 8 values).
+  __device__ __forceinline__ void issue_segment(int tile, int st) const {
+    const int row = tile / H, h = tile % H;
+    const int y = row % ny, z = row / ny + z0;
+    const int W = nx / H, ws = staged_width(nx, H);
+    const unsigned bar = smem_addr(&bars[st]);
+    T* dst = rows + (size_t)st * kPop * ws;
+    const unsigned seg = (unsigned)W * sizeof(T), halo = (unsigned)kHalo * sizeof(T);
+    if (lane == 0) mbar_expect_tx(bar, kPop * (ODD ? seg + 2 * halo : seg));
+    __syncwarp();
+    if (stall) return;
+    if (!ODD) {
+      for (int s = lane; s < kPop; s += 32)
+        bulk_load(smem_addr(dst + s * ws + kHalo),
+                  state + (size_t)s * n3 + ((long long)z * ny + y) * nx + (long long)h * W, seg, bar);
+    } else {
+      // two copies per storage slot: the segment with the halo inside the
+      // row, and the halo across the row's end (the first segment's left
+      // halo is the row's last kHalo values, the last segment's right halo
+      // its first ones)
+      for (int j = lane; j < 2 * kPop; j += 32) {
+        const int s = j >> 1, r = s / 3;
+        const int ys = wrap(y + run_dy(r), ny), zs = wrap(z + run_dz(r), nz);
+        const T* src = state + (size_t)s * n3 + ((long long)zs * ny + ys) * nx;
+        T* d = dst + s * ws;
+        if (h == 0) {
+          if (j & 1) bulk_load(smem_addr(d), src + (nx - kHalo), halo, bar);
+          else bulk_load(smem_addr(d + kHalo), src, seg + halo, bar);
+        } else {
+          if (j & 1) bulk_load(smem_addr(d + kHalo + W), src, halo, bar);
+          else bulk_load(smem_addr(d), src + (W - kHalo), seg + halo, bar);
+        }
       }
     }
   }
@@ -594,21 +659,25 @@ struct RowIO {
 };
 
 // Launch bounds per instantiation: 128 registers per thread (512 threads'
-// worth per SM).
-constexpr int row_bound_threads(int nx) { return nx ? nx / 2 : kRowMaxThreads; }
-constexpr int row_bound_blocks(int nx) { return 512 / row_bound_threads(nx); }
+// worth per SM); a block has nx / (2 H) threads.
+constexpr int row_bound_threads(int nx, int H = 1) { return nx ? nx / (2 * H) : kRowMaxThreads; }
+constexpr int row_bound_blocks(int nx, int H = 1) { return 512 / row_bound_threads(nx, H); }
 
 // Bfd: the pre-collision B - B_ref ([3][N3], storage type), read by kVarFdCurrent only.
-template <class T, bool ODD, int NX, int kRowStages, int VAR>
-__global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
+// H: segments per row (1: a tile is a whole row; 2: half a row, rows of
+// more than 256 sites only).
+template <class T, bool ODD, int NX, int kRowStages, int VAR, int H = 1>
+__global__ void __launch_bounds__(row_bound_threads(NX, H), row_bound_blocks(NX, H))
     step_row_kernel(T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
                     const T* __restrict__ Bfd, const __grid_constant__ RowMaps maps, RowWait wt) {
+  static_assert(H == 1 || (H == 2 && kRowStages == 2 && (NX == 0 || NX > 256)), "half rows: long rows, two stages");
   extern __shared__ __align__(128) unsigned char smem[];
   const int nx = NX ? NX : g.nx, ny = g.ny, nz = g.nz;
   const unsigned rowbytes = static_cast<unsigned>(nx) * sizeof(T);
-  T* rows = reinterpret_cast<T*>(smem);  // [stage][48 storage slots][nx]
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kRowStages * kPop * rowbytes);
-  const int ntiles = ny * g.nzi;  // rows of the updated planes
+  const unsigned stagebytes = static_cast<unsigned>(kPop * staged_width(nx, H) * sizeof(T));
+  T* rows = reinterpret_cast<T*>(smem);  // [stage][48 storage slots][staged_width(nx, H)]
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kRowStages * stagebytes);
+  const int ntiles = ny * g.nzi * H;  // rows (or row segments) of the updated planes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool boxed = nx <= kBoxMaxX;
 
@@ -618,7 +687,8 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
   }
   __syncthreads();
 
-  const RowIO<T, ODD> io{state, rows, bars, g.n3, nx, ny, nz, g.z0, rowbytes, lane, boxed, wt.stall != 0, &maps};
+  const RowIO<T, ODD, H> io{state, rows, bars, g.n3, nx, ny, nz, g.z0, rowbytes, lane, boxed && H == 1,
+                           wt.stall != 0, &maps};
 
   const int first = blockIdx.x, stride = gridDim.x;
   // Tiles staged before the loop: both stages with two; with three, two of
@@ -631,7 +701,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
   // it also beats three stages of three blocks: 32.15 -> 32.9; at 512-site
   // rows, where a stage is 48 KB and the refill needs its lead time, it was
   // slower: 29.4 -> 28.4).
-  constexpr bool kMidRefill = kRowStages == 2 && NX != 0 && NX <= 256;
+  constexpr bool kMidRefill = kRowStages == 2 && NX != 0 && NX <= 256 && H == 1;
   // Rows longer than 256 sites (two stages of up to 96 KB): the results go
   // straight from registers to HBM and the staged rows are only read, so a
   // stage is refilled as soon as its tile's collision ends, with no store to
@@ -639,7 +709,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
   // +4 %; at 256-site rows the extra address arithmetic made it slower).  No
   // location is read or written by more than one tile, so the order of these
   // stores and of other tiles' loads does not matter.
-  constexpr bool kDirect = kRowStages == 2 && (NX == 512 || NX == 0);
+  constexpr bool kDirect = kRowStages == 2 && (NX == 512 || NX == 0 || H > 1);
   if (warp == 0)
     for (int s = 0; s < kAhead; ++s)
       if (first + s * stride < ntiles) io.issue(first + s * stride, s);
@@ -655,7 +725,17 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
       // this pair read that slot from, so each thread writes only what it
       // has read, and every staged row is the new content of the HBM row it
       // was loaded from.
-      const PairAccess<T, ODD, NX> A(rows + (size_t)st * kPop * nx, nx);
+      const PairAccess<T, ODD, NX, H> A(rows + (size_t)st * (stagebytes / sizeof(T)), nx);
+      // the pair's sites in the row (global x), for the direct stores and the
+      // B field: the staged positions for whole rows, shifted by the
+      // segment's first site for half rows
+      int gx0 = A.x0, gx1 = A.x1, gxm0 = A.xm0, gxp1 = A.xp1;
+      if constexpr (H > 1) {
+        gx0 = (tile % H) * (nx / H) + 2 * (int)threadIdx.x;
+        gx1 = gx0 + 1;
+        gxm0 = gx0 == 0 ? nx - 1 : gx0 - 1;
+        gxp1 = gx1 == nx - 1 ? 0 : gx1 + 1;
+      }
       auto ldf = [&](int px, int py, int pz) {
         const int q = px + 3 * py + 9 * pz;
         return A.ld(ODD ? 26 - q : q, 1 - px);
@@ -663,13 +743,13 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
       auto ldg = [&](int c, int i) { return A.ld(kQ + 3 * (ODD ? opp7(i) : i) + c, -mx7(i)); };
       PairGlobal<T, ODD> G;
       if constexpr (kDirect) {
-        const int y = tile % ny, z = tile / ny + g.z0;
+        const int y = (tile / H) % ny, z = (tile / H) / ny + g.z0;
         G.state = state;
         G.n3 = g.n3;
-        G.x0 = A.x0;
-        G.x1 = A.x1;
-        G.xm0 = A.xm0;
-        G.xp1 = A.xp1;
+        G.x0 = gx0;
+        G.x1 = gx1;
+        G.xm0 = gxm0;
+        G.xp1 = gxp1;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           G.yo[k] = wrap(y + k - 1, ny) * nx;
@@ -688,7 +768,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
       // J = periodic central-difference curl of the pre-collision field at
       // the pair (the face neighbours in y and z are whole-pair loads).
       auto curl_b = [&](f2 (&J)[3]) {
-        const int y = tile % ny, z = tile / ny + g.z0;
+        const int y = (tile / H) % ny, z = (tile / H) / ny + g.z0;
         const long long r0 = ((long long)z * ny + y) * nx;
         const long long ryp = ((long long)z * ny + wrap(y + 1, ny)) * nx;
         const long long rym = ((long long)z * ny + wrap(y - 1, ny)) * nx;
@@ -696,12 +776,12 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
         const long long rzm = ((long long)wrap(z - 1, nz) * ny + y) * nx;
         const T *Bx = Bfd, *By = Bfd + g.n3, *Bz = Bfd + 2 * g.n3;
         // the pair (x0, x1) of a row as one 32-bit load, a single value as one 16-bit load
-        auto at = [&](const T* b, long long r) { return f2{dec2(b + r + A.x0)}; };
+        auto at = [&](const T* b, long long r) { return f2{dec2(b + r + gx0)}; };
         auto one = [&](const T* b, long long i) { return Codec<T>::dec(b[i]); };
         const f2 by0 = at(By, r0), bz0 = at(Bz, r0);
         // B(x + 1) - B(x - 1) at x = x0, x1
-        const f2 dxBy = pack(by0.v.y, one(By, r0 + A.xp1)) - pack(one(By, r0 + A.xm0), by0.v.x);
-        const f2 dxBz = pack(bz0.v.y, one(Bz, r0 + A.xp1)) - pack(one(Bz, r0 + A.xm0), bz0.v.x);
+        const f2 dxBy = pack(by0.v.y, one(By, r0 + gxp1)) - pack(one(By, r0 + gxm0), by0.v.x);
+        const f2 dxBz = pack(bz0.v.y, one(Bz, r0 + gxp1)) - pack(one(Bz, r0 + gxm0), bz0.v.x);
         J[0] = 0.5f * ((at(Bz, ryp) - at(Bz, rym)) - (at(By, rzp) - at(By, rzm)));
         J[1] = 0.5f * ((at(Bx, rzp) - at(Bx, rzm)) - dxBz);
         J[2] = 0.5f * (dxBy - (at(Bx, ryp) - at(Bx, rym)));
@@ -748,8 +828,8 @@ __global__ void __launch_bounds__(row_bound_threads(NX), row_bound_blocks(NX))
   if (warp == 0) bulk_wait_done();
 }
 
-size_t row_smem_bytes(int nx, size_t elem, int stages) {
-  return stages * (kPop * (size_t)nx * elem + sizeof(unsigned long long));
+size_t row_smem_bytes(int nx, size_t elem, int stages, int H = 1) {
+  return stages * (kPop * (size_t)staged_width(nx, H) * elem + sizeof(unsigned long long));
 }
 
 // Stages per row length, from timings at 128^3, 256^3 and 512^3 (FP16).
@@ -767,11 +847,11 @@ constexpr int row_stages(int nx) { return nx > 128 && nx < 256 ? 3 : 2; }
 // and on nx only); a mutex makes concurrent host threads safe.
 constexpr int kMaxDevices = 64;
 
-template <class T, bool ODD, int NX, int S, int VAR>
+template <class T, bool ODD, int NX, int S, int VAR, int H>
 cudaError_t row_config(const Grid& g, int* grid, size_t* smem_out) {
-  auto kern = step_row_kernel<T, ODD, NX, S, VAR>;
-  const int threads = g.nx / 2;
-  const size_t smem = row_smem_bytes(g.nx, sizeof(T), S);
+  auto kern = step_row_kernel<T, ODD, NX, S, VAR, H>;
+  const int threads = g.nx / (2 * H);
+  const size_t smem = row_smem_bytes(g.nx, sizeof(T), S, H);
   struct Cache {
     size_t attr_smem, occ_smem;
     int occ, nsm;
@@ -796,28 +876,32 @@ cudaError_t row_config(const Grid& g, int* grid, size_t* smem_out) {
     c.occ_smem = smem;
   }
   if (c.nsm == 0 && (e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const long long ntiles = (long long)g.ny * g.nzi, slots = (long long)c.occ * c.nsm;
+  const long long ntiles = (long long)g.ny * g.nzi * H, slots = (long long)c.occ * c.nsm;
   *grid = (int)(ntiles < slots ? ntiles : slots);
   *smem_out = smem;
   return cudaSuccess;
 }
 
-template <class T, bool ODD, int NX, int S, int VAR>
+template <class T, bool ODD, int NX, int S, int VAR, int H = 1>
 cudaError_t row_launch(const RowCall& c) {
   int grid = 0;
   size_t smem = 0;
-  cudaError_t e = row_config<T, ODD, NX, S, VAR>(c.g, &grid, &smem);
+  cudaError_t e = row_config<T, ODD, NX, S, VAR, H>(c.g, &grid, &smem);
   RowMaps maps{};
-  if (e == cudaSuccess && c.g.nx <= kBoxMaxX) e = row_maps(c.pop, c.g, &maps);
+  if (e == cudaSuccess && H == 1 && c.g.nx <= kBoxMaxX) e = row_maps(c.pop, c.g, &maps);
   if (e != cudaSuccess || !c.launch) return e;
-  step_row_kernel<T, ODD, NX, S, VAR>
-      <<<grid, c.g.nx / 2, smem, c.s>>>(static_cast<T*>(c.pop), c.g, c.k, c.flag, static_cast<const T*>(c.Bfd),
-                                        maps, c.wt);
+  step_row_kernel<T, ODD, NX, S, VAR, H>
+      <<<grid, c.g.nx / (2 * H), smem, c.s>>>(static_cast<T*>(c.pop), c.g, c.k, c.flag,
+                                              static_cast<const T*>(c.Bfd), maps, c.wt);
   return cudaGetLastError();
 }
 
 template <class T, bool ODD, int VAR>
 cudaError_t row_nx(const RowCall& c) {
+  if (c.segments == 2) {
+    if (c.g.nx <= kBoxMaxX) return cudaErrorInvalidValue;
+    return c.g.nx == 512 ? row_launch<T, ODD, 512, 2, VAR, 2>(c) : row_launch<T, ODD, 0, 2, VAR, 2>(c);
+  }
   switch (c.g.nx) {
     case 64: return row_launch<T, ODD, 64, row_stages(64), VAR>(c);
     case 128: return row_launch<T, ODD, 128, row_stages(128), VAR>(c);

@@ -269,3 +269,84 @@ def test_row_kernel_variant_graph_replay_is_bit_identical(variant):
         b.step(n)
     assert torch.equal(a.populations(), b.populations())
     assert a.sync() is None and b.sync() is None
+
+
+# Half rows per tile (kernel "row_half", rows longer than 256 sites): the
+# segment's halos replace the whole row's wrap-around, the results go
+# straight to HBM; the per-site arithmetic is the same, so the populations
+# must equal the whole-row tiling's bit for bit.
+HALF_SHAPES = [(2, 3, 320), (2, 2, 512), (1, 2, 576), (2, 1, 640), (1, 1, 960), (2, 1, 1024)]
+
+
+@pytest.mark.parametrize("shape", HALF_SHAPES)
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_half_rows_equal_whole_rows(shape, storage):
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    nz, ny, nx = shape
+    u, B = _fields(shape, 57)
+    sims = [Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), kernel=k)
+            for k in ("row", "row_half")]
+    for s in sims:
+        s.init(None, u, B)
+    for n in (3, 4):  # an odd step count, then an even one
+        for s in sims:
+            s.step(n)
+        assert torch.equal(sims[0].populations(), sims[1].populations())
+    for s in sims:
+        assert s.sync() is None
+        s.close()
+
+
+@pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
+def test_half_rows_equal_whole_rows_variants(variant):
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    shape = (2, 3, 512)
+    nz, ny, nx = shape
+    u, B = _fields(shape, 59)
+    sims = [Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0), kernel=k, variant=variant)
+            for k in ("row", "row_half")]
+    for s in sims:
+        s.init(None, u, B)
+        s.step(7)
+    assert torch.equal(sims[0].populations(), sims[1].populations())
+    for s in sims:
+        s.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 2, 576), (2, 1, 640)])
+def test_half_rows_vs_oracle(shape):
+    """The row lengths where whole rows leave too few warps per SM, on half
+    rows, against the oracle at the row kernel's FP16 bounds."""
+    u, B = _fields(shape, 41)
+    fg, mg, fo, mo = run_both(shape, 0.52, 0.55, 1.5, u, B, 21, storage="fp16", literal=False, Bref=tuple(B0),
+                              kernel="row_half")
+    _check_vs_oracle(shape, fg, mg, fo, mo, TOL["fp16"])
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 512), (1, 2, 576)])
+def test_wait_limit_on_half_rows(shape):
+    """The bounded waits of the half-row pipeline: a stalled step reports
+    FLAME_ERR_TIMEOUT and leaves the state as it was."""
+    import torch
+    from paper_2212_11024_gb300 import Flame, FlameError
+    from paper_2212_11024_gb300.flame import FLAME_ERR_TIMEOUT
+    nz, ny, nx = shape
+    u, B = _fields(shape, 61)
+    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0), kernel="row_half")
+    sim.init(None, u, B)
+    sim.step(3)
+    blob0 = sim.get_state()[0]
+    sim.debug_stall_next_step(256)
+    with pytest.raises(FlameError) as e:
+        sim.step(1)
+    assert e.value.status == FLAME_ERR_TIMEOUT
+    import ctypes
+    from paper_2212_11024_gb300.flame import library
+    blob1 = torch.empty_like(blob0)
+    st, pa = ctypes.c_longlong(), ctypes.c_int()
+    library().flame_get_state(sim._ctx, ctypes.c_void_p(blob1.data_ptr()), ctypes.byref(st), ctypes.byref(pa))
+    torch.cuda.synchronize()
+    assert torch.equal(blob0, blob1) and st.value == 3
+    sim.close()
