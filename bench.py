@@ -92,8 +92,10 @@ def parse_variant(spec):
 
 def kernel_name(storage, kernel, n):
     """The step kernel flame_step launches for this storage at n^3."""
-    if kernel == "auto" and storage in ("fp16", "bf16") and n % 64 == 0 and 64 <= n <= 1024 and n not in (576, 640):
-        return f"step_row_kernel<{storage}> (TMA-staged x rows, packed FP32 pairs)"
+    if kernel == "auto" and storage in ("fp16", "bf16") and n % 64 == 0 and 64 <= n <= 1024:
+        if n in (576, 640):
+            return f"step_row_kernel<{storage}> (half x rows staged by bulk copies, packed FP32 pairs)"
+        return f"step_row_kernel<{storage}> (staged x rows, packed FP32 pairs)"
     return f"step_kernel<{storage}> (one site per thread)"
 
 

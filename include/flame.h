@@ -103,14 +103,14 @@ typedef struct {
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
     int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant), nx a
-                         multiple of 64 in 64..1024 other than 576 and 640 (the row
-                         lengths where it was timed faster) and a 16-byte aligned state
-                         use the row kernel (x rows staged in shared memory, two sites
-                         per thread in packed FP32 pairs), everything else the one-site
-                         kernel; 1: always the one-site kernel; 2: the row kernel with a
-                         whole row per block tile, 3: with half a row per tile (rows of
-                         more than 256 sites), where the row kernel applies, else the
-                         one-site kernel.  All compute the same step in FP32; results
+                         multiple of 64 in 64..1024 and a 16-byte aligned state use the
+                         row kernel (x rows staged in shared memory, two sites per thread
+                         in packed FP32 pairs; half a row per tile at 576 and 640 sites,
+                         a whole row elsewhere: the faster tilings as timed), everything
+                         else the one-site kernel; 1: always the one-site kernel; 2: the
+                         row kernel with a whole row per block tile, 3: with half a row
+                         per tile (rows of more than 256 sites), where the row kernel
+                         applies, else the one-site kernel.  All compute the same step in FP32; results
                          agree to FP32 rounding before encoding (the row kernel's tilings
                          agree bit for bit). */
     int halo_z;       /* 0: a periodic nx x ny x nz lattice.  1: one z-slab of a larger
