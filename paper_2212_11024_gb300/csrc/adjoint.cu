@@ -132,10 +132,18 @@ __device__ __forceinline__ void block_sum_to(double v, double* out) {
   }
 }
 
+// Base pointers of lambda_{t+1} (in) and lambda_t (out) per natural slot,
+// passed as kernel parameters (as the state's Slots are), so that each of a
+// site's 96 lambda accesses is one index computation on a parameter.
+struct LamSlots {
+  const float* in[kPop];
+  float* out[kPop];
+};
+
 template <class T, bool ODD>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
-    adjoint_step_kernel(Slots<T> P, Grid g, StepConsts k, const float* __restrict__ lam_in,
-                        float* __restrict__ lam_out, double* __restrict__ partials) {
+    adjoint_step_kernel(Slots<T> P, Grid g, StepConsts k, const __grid_constant__ LamSlots L,
+                        double* __restrict__ partials) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z + g.z0;
@@ -151,12 +159,12 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
     float lf[kQ], lg[3][kM];
     auto gather = [&]() {
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) lf[i] = lam_in[(long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))];
+      for (int i = 0; i < kQ; ++i) lf[i] = L.in[i][site + nb(cx27(i), cy27(i), cz27(i))];
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int i = 0; i < kM; ++i)
-          lg[b][i] = lam_in[(long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))];
+          lg[b][i] = L.in[mslot(b, i)][site + nb(mx7(i), my7(i), mz7(i))];
     };
     if constexpr (adj_early_gather<T>()) gather();
 
@@ -468,9 +476,9 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
         }
         if (cx * cy != 0) base += cx * cy > 0 ? Sb[0][1] : -Sb[0][1];
         const float side = base + Sb[2][2];
-        lam_out[(long long)idx27(px, py, 0) * n3 + site] = side - lin;
-        lam_out[(long long)idx27(px, py, 1) * n3 + site] = base;
-        lam_out[(long long)idx27(px, py, 2) * n3 + site] = side + lin;
+        L.out[idx27(px, py, 0)][site] = side - lin;
+        L.out[idx27(px, py, 1)][site] = base;
+        L.out[idx27(px, py, 2)][site] = side + lin;
       }
 #pragma unroll
     for (int b = 0; b < 3; ++b)
@@ -481,7 +489,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
           const int a = (i - 1) >> 1;
           v += (i & 1) ? Lb[a][b] : -Lb[a][b];
         }
-        lam_out[(long long)mslot(b, i) * n3 + site] = v;
+        L.out[mslot(b, i)][site] = v;
       }
     abar_site = (double)abar;
   }
@@ -642,10 +650,15 @@ cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, con
                       double* partials, long long nblk, double* ddi, cudaStream_t s) {
   const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
   const Slots<T> P = make_slots<T>(pop, g);
+  LamSlots L;
+  for (int q = 0; q < kPop; ++q) {
+    L.in[q] = lin + (size_t)q * (size_t)g.n3;
+    L.out[q] = lout + (size_t)q * (size_t)g.n3;
+  }
   if (odd)
-    adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, lin, lout, partials);
+    adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, L, partials);
   else
-    adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, lin, lout, partials);
+    adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, L, partials);
   sum_partials_kernel<<<1, 256, 0, s>>>(partials, nblk, ddi);
   return cudaGetLastError();
 }
