@@ -134,15 +134,24 @@ __device__ __forceinline__ void block_sum_to(double v, double* out) {
 
 // Base pointers of lambda_{t+1} (in) and lambda_t (out) per natural slot,
 // passed as kernel parameters (as the state's Slots are), so that each of a
-// site's 96 lambda accesses is one index computation on a parameter.
+// site's 96 lambda accesses is one index computation on a parameter.  With
+// 16-bit storage this gave 9.5 -> 10.1 GLUPS at 256^3 (128 registers and no
+// spills instead of 20 bytes); with FP32 storage, whose lambda gather is
+// issued with the state loads, it ran slower (9.2 -> 8.05), so FP32 storage
+// indexes lambda from its base address (lam_slot_pointers<T>()).
 struct LamSlots {
   const float* in[kPop];
   float* out[kPop];
 };
+template <class T>
+__host__ __device__ constexpr bool lam_slot_pointers() {
+  return sizeof(T) == 2;
+}
 
 template <class T, bool ODD>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
     adjoint_step_kernel(Slots<T> P, Grid g, StepConsts k, const __grid_constant__ LamSlots L,
+                        const float* __restrict__ lam_in, float* __restrict__ lam_out,
                         double* __restrict__ partials) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -159,12 +168,15 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
     float lf[kQ], lg[3][kM];
     auto gather = [&]() {
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) lf[i] = L.in[i][site + nb(cx27(i), cy27(i), cz27(i))];
+      for (int i = 0; i < kQ; ++i)
+        lf[i] = lam_slot_pointers<T>() ? L.in[i][site + nb(cx27(i), cy27(i), cz27(i))]
+                                       : lam_in[(long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))];
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int i = 0; i < kM; ++i)
-          lg[b][i] = L.in[mslot(b, i)][site + nb(mx7(i), my7(i), mz7(i))];
+          lg[b][i] = lam_slot_pointers<T>() ? L.in[mslot(b, i)][site + nb(mx7(i), my7(i), mz7(i))]
+                                            : lam_in[(long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))];
     };
     if constexpr (adj_early_gather<T>()) gather();
 
@@ -476,9 +488,12 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
         }
         if (cx * cy != 0) base += cx * cy > 0 ? Sb[0][1] : -Sb[0][1];
         const float side = base + Sb[2][2];
-        L.out[idx27(px, py, 0)][site] = side - lin;
-        L.out[idx27(px, py, 1)][site] = base;
-        L.out[idx27(px, py, 2)][site] = side + lin;
+        float* o0 = lam_slot_pointers<T>() ? L.out[idx27(px, py, 0)] : lam_out + (long long)idx27(px, py, 0) * n3;
+        float* o1 = lam_slot_pointers<T>() ? L.out[idx27(px, py, 1)] : lam_out + (long long)idx27(px, py, 1) * n3;
+        float* o2 = lam_slot_pointers<T>() ? L.out[idx27(px, py, 2)] : lam_out + (long long)idx27(px, py, 2) * n3;
+        o0[site] = side - lin;
+        o1[site] = base;
+        o2[site] = side + lin;
       }
 #pragma unroll
     for (int b = 0; b < 3; ++b)
@@ -489,7 +504,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
           const int a = (i - 1) >> 1;
           v += (i & 1) ? Lb[a][b] : -Lb[a][b];
         }
-        L.out[mslot(b, i)][site] = v;
+        (lam_slot_pointers<T>() ? L.out[mslot(b, i)] : lam_out + (long long)mslot(b, i) * n3)[site] = v;
       }
     abar_site = (double)abar;
   }
@@ -656,9 +671,9 @@ cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, con
     L.out[q] = lout + (size_t)q * (size_t)g.n3;
   }
   if (odd)
-    adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, L, partials);
+    adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, L, lin, lout, partials);
   else
-    adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, L, partials);
+    adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, L, lin, lout, partials);
   sum_partials_kernel<<<1, 256, 0, s>>>(partials, nblk, ddi);
   return cudaGetLastError();
 }
