@@ -31,24 +31,16 @@
 namespace flame {
 namespace {
 
-// 128-thread blocks.  The step adjoint keeps much of a site's transposed
-// Jacobian live and waits on its loads.  With 16-bit storage four blocks per
-// SM (16 warps, 128 registers, ~20 bytes of spills) beat three of 168
-// registers by 13 %; with FP32 storage three blocks that issue the lambda
-// gather together with the state loads (before the forward recompute, so the
-// two latencies overlap; 168 registers, no spills) beat four blocks with the
-// gather after the recompute by 6 % (and one 256-thread block of 185
-// registers by 1.6x).  Issuing the gather early with four blocks, or with
-// 16-bit storage, was slower.
+// 128-thread blocks, four per SM (128 registers, no spills), the lambda
+// gather issued after the forward recompute, and lambda's slot base pointers
+// as kernel parameters (LamSlots).  Timed at 256^3 (GLUPS FP32 / FP16):
+// one 256-thread block of 185 registers per SM with per-velocity sums 5.6 /
+// 5.3; 1-D passes, 128 x 3 (168 registers) 8.30 / 8.53; 128 x 4 with lambda
+// indexed from its base 8.73 / 9.60 (20 bytes of spills); FP32 with the
+// gather issued with the state loads, 128 x 3, 9.22; slot pointers, 128 x 4
+// (no spills) 9.37 / 10.1.
 constexpr int kAdjThreads = 128;
-template <class T>
-__host__ __device__ constexpr bool adj_early_gather() {
-  return sizeof(T) == 4;
-}
-template <class T>
-__host__ __device__ constexpr int adj_min_blocks() {
-  return adj_early_gather<T>() ? 3 : 4;
-}
+constexpr int kAdjMinBlocks = 4;
 
 // 1-D functions of the undivided equilibrium and inverse-moment maps, and
 // their derivatives in u, at velocity component c (index p = c + 1).
@@ -134,24 +126,15 @@ __device__ __forceinline__ void block_sum_to(double v, double* out) {
 
 // Base pointers of lambda_{t+1} (in) and lambda_t (out) per natural slot,
 // passed as kernel parameters (as the state's Slots are), so that each of a
-// site's 96 lambda accesses is one index computation on a parameter.  With
-// 16-bit storage this gave 9.5 -> 10.1 GLUPS at 256^3 (128 registers and no
-// spills instead of 20 bytes); with FP32 storage, whose lambda gather is
-// issued with the state loads, it ran slower (9.2 -> 8.05), so FP32 storage
-// indexes lambda from its base address (lam_slot_pointers<T>()).
+// site's 96 lambda accesses is one index computation on a parameter.
 struct LamSlots {
   const float* in[kPop];
   float* out[kPop];
 };
-template <class T>
-__host__ __device__ constexpr bool lam_slot_pointers() {
-  return sizeof(T) == 2;
-}
 
 template <class T, bool ODD>
-__global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
+__global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
     adjoint_step_kernel(Slots<T> P, Grid g, StepConsts k, const __grid_constant__ LamSlots L,
-                        const float* __restrict__ lam_in, float* __restrict__ lam_out,
                         double* __restrict__ partials) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -161,24 +144,19 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
   if (live) {
     const int site = (z * g.ny + y) * g.nx + x;
     const Nbr nb = make_nbr(x, y, z, g);
-    const long long n3 = g.n3;
 
-    // ---- gather dL/df* (streaming transpose: from x + c_q), before or after
-    // the forward recompute (adj_early_gather)
+    // ---- gather dL/df* (streaming transpose: from x + c_q), issued after the
+    // forward recompute
     float lf[kQ], lg[3][kM];
     auto gather = [&]() {
 #pragma unroll
-      for (int i = 0; i < kQ; ++i)
-        lf[i] = lam_slot_pointers<T>() ? L.in[i][site + nb(cx27(i), cy27(i), cz27(i))]
-                                       : lam_in[(long long)i * n3 + site + nb(cx27(i), cy27(i), cz27(i))];
+      for (int i = 0; i < kQ; ++i) lf[i] = L.in[i][site + nb(cx27(i), cy27(i), cz27(i))];
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int i = 0; i < kM; ++i)
-          lg[b][i] = lam_slot_pointers<T>() ? L.in[mslot(b, i)][site + nb(mx7(i), my7(i), mz7(i))]
-                                            : lam_in[(long long)mslot(b, i) * n3 + site + nb(mx7(i), my7(i), mz7(i))];
+          lg[b][i] = L.in[mslot(b, i)][site + nb(mx7(i), my7(i), mz7(i))];
     };
-    if constexpr (adj_early_gather<T>()) gather();
 
     // ---- forward recompute (deviation variables, as in the step kernel)
     float sf[kQ];
@@ -275,7 +253,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
         for (int b = a; b < 3; ++b) D[a][b] = r * (a == b ? S[a][b] - tr3 : S[a][b]);
     }
 
-    if constexpr (!adj_early_gather<T>()) gather();
+    gather();
 
     // ---- magnetic collision
     const float omB = k.omegaB;
@@ -488,12 +466,9 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
         }
         if (cx * cy != 0) base += cx * cy > 0 ? Sb[0][1] : -Sb[0][1];
         const float side = base + Sb[2][2];
-        float* o0 = lam_slot_pointers<T>() ? L.out[idx27(px, py, 0)] : lam_out + (long long)idx27(px, py, 0) * n3;
-        float* o1 = lam_slot_pointers<T>() ? L.out[idx27(px, py, 1)] : lam_out + (long long)idx27(px, py, 1) * n3;
-        float* o2 = lam_slot_pointers<T>() ? L.out[idx27(px, py, 2)] : lam_out + (long long)idx27(px, py, 2) * n3;
-        o0[site] = side - lin;
-        o1[site] = base;
-        o2[site] = side + lin;
+        L.out[idx27(px, py, 0)][site] = side - lin;
+        L.out[idx27(px, py, 1)][site] = base;
+        L.out[idx27(px, py, 2)][site] = side + lin;
       }
 #pragma unroll
     for (int b = 0; b < 3; ++b)
@@ -504,7 +479,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<T>())
           const int a = (i - 1) >> 1;
           v += (i & 1) ? Lb[a][b] : -Lb[a][b];
         }
-        (lam_slot_pointers<T>() ? L.out[mslot(b, i)] : lam_out + (long long)mslot(b, i) * n3)[site] = v;
+        L.out[mslot(b, i)][site] = v;
       }
     abar_site = (double)abar;
   }
@@ -671,9 +646,9 @@ cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, con
     L.out[q] = lout + (size_t)q * (size_t)g.n3;
   }
   if (odd)
-    adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, L, lin, lout, partials);
+    adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, L, partials);
   else
-    adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, L, lin, lout, partials);
+    adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, L, partials);
   sum_partials_kernel<<<1, 256, 0, s>>>(partials, nblk, ddi);
   return cudaGetLastError();
 }
