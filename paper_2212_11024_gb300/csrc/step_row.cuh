@@ -514,30 +514,38 @@ struct PairAccess {
   }
 };
 
+// Base of every storage slot's rows (slot s starts at state + s N3), a
+// kernel parameter, for the direct stores of long rows.
+template <class T>
+struct SlotBases {
+  T* p[kPop];
+};
+
 // Results of a pair written straight to HBM (rows longer than 256 sites):
 // storage slot s was staged from the row (y, z) + (run_dy(s / 3),
 // run_dz(s / 3)) on odd steps and from (y, z) on even steps, and a result
 // goes to the position of that row it was read from (as st() above does in
-// the staged copy).  yo / zo: the row offsets of y - 1, y, y + 1 and of the
-// planes z - 1, z, z + 1 (periodic).
+// the staged copy).  off[dz + 1][dy + 1]: the offset of the row (y + dy,
+// z + dz) (periodic) plus the pair's first site x0, so that a store is one
+// address computation on the slot's base; dm = xm0 - x0 and dp = xp1 - x1
+// are the shifted sites' offsets (the wrap at the row's ends).
 template <class T, bool ODD>
 struct PairGlobal {
-  T* state;
-  long long n3;
-  int x0, x1, xm0, xp1;
-  int yo[3], zo[3];
+  const SlotBases<T>* base;
+  int off[3][3];
+  int dm, dp;
   __device__ __forceinline__ void st(int s, int d, f2 v) const {
     const int r = s / 3;
     const int dy = ODD ? run_dy(r) : 0, dz = ODD ? run_dz(r) : 0;
-    T* row = state + (long long)s * n3 + (zo[dz + 1] + yo[dy + 1]);
+    T* row = base->p[s] + off[dz + 1][dy + 1];
     if (!ODD || d == 0) {
-      Codec2<T>::enc(row + x0, v);
+      Codec2<T>::enc(row, v);
     } else if (d < 0) {
-      row[xm0] = Codec<T>::enc(v.v.x);
-      row[x0] = Codec<T>::enc(v.v.y);
+      row[dm] = Codec<T>::enc(v.v.x);
+      row[0] = Codec<T>::enc(v.v.y);
     } else {
-      row[x1] = Codec<T>::enc(v.v.x);
-      row[xp1] = Codec<T>::enc(v.v.y);
+      row[1] = Codec<T>::enc(v.v.x);
+      row[1 + dp] = Codec<T>::enc(v.v.y);
     }
   }
 };
@@ -669,7 +677,8 @@ constexpr int row_bound_blocks(int nx, int H = 1) { return 512 / row_bound_threa
 template <class T, bool ODD, int NX, int kRowStages, int VAR, int H = 1>
 __global__ void __launch_bounds__(row_bound_threads(NX, H), row_bound_blocks(NX, H))
     step_row_kernel(T* __restrict__ state, Grid g, StepConsts k, unsigned* __restrict__ flag,
-                    const T* __restrict__ Bfd, const __grid_constant__ RowMaps maps, RowWait wt) {
+                    const T* __restrict__ Bfd, const __grid_constant__ RowMaps maps,
+                    const __grid_constant__ SlotBases<T> bases, RowWait wt) {
   static_assert(H == 1 || (H == 2 && kRowStages == 2 && (NX == 0 || NX > 256)), "half rows: long rows, two stages");
   extern __shared__ __align__(128) unsigned char smem[];
   const int nx = NX ? NX : g.nx, ny = g.ny, nz = g.nz;
@@ -744,17 +753,16 @@ __global__ void __launch_bounds__(row_bound_threads(NX, H), row_bound_blocks(NX,
       PairGlobal<T, ODD> G;
       if constexpr (kDirect) {
         const int y = (tile / H) % ny, z = (tile / H) / ny + g.z0;
-        G.state = state;
-        G.n3 = g.n3;
-        G.x0 = gx0;
-        G.x1 = gx1;
-        G.xm0 = gxm0;
-        G.xp1 = gxp1;
+        G.base = &bases;
+        G.dm = gxm0 - gx0;
+        G.dp = gxp1 - gx1;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          G.yo[k] = wrap(y + k - 1, ny) * nx;
-          G.zo[k] = wrap(z + k - 1, nz) * ny * nx;
-        }
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+            G.off[dz][dy] = (ODD || (dz == 1 && dy == 1))
+                                ? (wrap(z + dz - 1, nz) * ny + wrap(y + dy - 1, ny)) * nx + gx0
+                                : 0;
       }
       auto stf = [&](int px, int py, int pz, f2 v) {
         const int q = px + 3 * py + 9 * pz;
@@ -890,9 +898,11 @@ cudaError_t row_launch(const RowCall& c) {
   RowMaps maps{};
   if (e == cudaSuccess && H == 1 && c.g.nx <= kBoxMaxX) e = row_maps(c.pop, c.g, &maps);
   if (e != cudaSuccess || !c.launch) return e;
+  SlotBases<T> bases;
+  for (int sl = 0; sl < kPop; ++sl) bases.p[sl] = static_cast<T*>(c.pop) + (size_t)sl * (size_t)c.g.n3;
   step_row_kernel<T, ODD, NX, S, VAR, H>
       <<<grid, c.g.nx / (2 * H), smem, c.s>>>(static_cast<T*>(c.pop), c.g, c.k, c.flag,
-                                              static_cast<const T*>(c.Bfd), maps, c.wt);
+                                              static_cast<const T*>(c.Bfd), maps, bases, c.wt);
   return cudaGetLastError();
 }
 
