@@ -49,17 +49,19 @@ cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 // Row lengths where the row kernel beats the one-site kernel, and with how
 // many segments per tile.  Timed with FP16 storage on ~4M-site lattices
 // (nx x m x m, GLUPS; whole rows / half rows / one-site): 256 31.9 / - /
-// 24.2, 320 27.7 / 18.6 / 21.0, 384 26.6 / 22.0 / 22.5, 448 27.6 / 21.9 /
-// 22.8, 512 29.1 / 25.4 / 24.3, 576 21.0 / 22.1 / 21.7, 640 23.1 / 24.3 /
-// 22.8, 704 25.0 / 20.9 / 23.2, 768 26.6 / 22.6 / 24.1, 832 24.6 / 22.2 /
-// 22.2, 896 26.3 / 23.7 / 22.9, 960 27.9 / 23.7 / 23.3, 1024 28.0 / 23.7 /
-// 22.9 (and 64-192 as in earlier timings: 28.0 / 24.1, 31.8 / 24.2, 29.4 /
-// 23.5 whole rows against one-site).  Whole rows win everywhere but at 576
-// and 640 sites, where a whole row's block of 288 / 320 threads with 96 KB
-// or more of stages fits once per SM; half rows (three blocks per SM) are
-// the faster tiling there.  Elsewhere half rows lose: twice the copies per
-// site (96 per tile on odd steps, the halo across a row's end by a copy of
-// its own) for the same warps per SM.
+// 24.2, 320 29.2 / 20.6 / 21.2, 384 26.6 / 22.0 / 22.5, 448 27.6 / 21.9 /
+// 22.8, 512 30.7 / 27.5 / 24.4, 576 21.9 / 24.4 / 21.9, 640 24.2 / 26.7 /
+// 23.0, 704 25.0 / 20.9 / 23.2, 768 27.8 / 24.6 / 24.3, 832 24.6 / 22.2 /
+// 22.2, 896 26.3 / 23.7 / 22.9, 960 27.9 / 23.7 / 23.3, 1024 29.3 / 26.5 /
+// 23.1 (384, 448 and 704-960 before the direct stores addressed their rows
+// from slot bases, which gained 5-8 % at 320-1024; 64-192 as in earlier
+// timings: 28.0 / 24.1, 31.8 / 24.2, 29.4 / 23.5 whole rows against
+// one-site).  Whole rows win everywhere but at 576 and 640 sites, where a
+// whole row's block of 288 / 320 threads with 96 KB or more of stages fits
+// once per SM; half rows per tile (three blocks per SM) are the faster
+// tiling there.  Elsewhere half rows lose: twice the copies per site (96 per
+// tile on odd steps, the halo across a row's end by a copy of its own) for
+// the same warps per SM.
 bool row_kernel_wins(int nx) { return true; }
 
 // Segments per tile of the automatic choice (kernel = 0).
