@@ -31,16 +31,25 @@
 namespace flame {
 namespace {
 
-// 128-thread blocks, four per SM (128 registers, no spills), the lambda
-// gather issued after the forward recompute, and lambda's slot base pointers
-// as kernel parameters (LamSlots).  Timed at 256^3 (GLUPS FP32 / FP16):
-// one 256-thread block of 185 registers per SM with per-velocity sums 5.6 /
-// 5.3; 1-D passes, 128 x 3 (168 registers) 8.30 / 8.53; 128 x 4 with lambda
-// indexed from its base 8.73 / 9.60 (20 bytes of spills); FP32 with the
-// gather issued with the state loads, 128 x 3, 9.22; slot pointers, 128 x 4
-// (no spills) 9.37 / 10.1.
-constexpr int kAdjThreads = 128;
-constexpr int kAdjMinBlocks = 4;
+// 64-thread blocks, ten per SM (96 registers, no spills).  The lambda gather
+// goes into shared memory by asynchronous copies (cp.async) that are in
+// flight during the forward recompute, and lambda is read from there where
+// it is used rather than held in registers; for 16-bit storage the state
+// loads are issued before the copies, for FP32 after them.  The d_i
+// contributions are summed per warp in FP64 (no block barrier) and the
+// partials added in a fixed order by two small kernels.  Timed at
+// 256^3 (GLUPS FP32 / FP16 storage): one 256-thread block of 185 registers
+// per SM with per-velocity sums 5.6 / 5.3; 1-D passes, 128 x 3 (168
+// registers) 8.30 / 8.53; lambda gathered into registers after the
+// recompute, 128 x 4, 9.37 / 10.1; gathered by cp.async 9.71 / 10.1; lambda
+// read from shared memory where used, 128 x 5, 9.71 / 10.39 (128 x 6, 80
+// registers with spills: 9.26 / 9.85); the partials summed by one block had
+// cost ~5 %: 10.23 / 10.91 with the two-level sum, 10.27 / 11.0 with the
+// per-storage load order and 64 x 10.  (Per-warp sums in FP32 gained 0.7 %
+// but, where the sites' terms cancel -- a random lambda: sum |a| / |sum a|
+// ~ 5000 -- they added ~5x the rounding of the per-site arithmetic to d_i.)
+constexpr int kAdjThreads = 64;
+constexpr int kAdjMinBlocks = 10;
 
 // 1-D functions of the undivided equilibrium and inverse-moment maps, and
 // their derivatives in u, at velocity component c (index p = c + 1).
@@ -110,6 +119,13 @@ __device__ __forceinline__ float zpass(const float (&y)[3], F f) {
   return app(f, y[0], y[1], y[2]);
 }
 
+// Per-warp partial sums (no block barrier at the end of the step kernel);
+// blocks are whole warps (site_block rounds x to 32).
+__device__ __forceinline__ void warp_sum_to(double v, double* out) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) *out = v;
+}
+
 __device__ __forceinline__ void block_sum_to(double v, double* out) {
   __shared__ double sh[32];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -123,6 +139,18 @@ __device__ __forceinline__ void block_sum_to(double v, double* out) {
     *out = a;
   }
 }
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ float lds(const float* p) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Base pointers of lambda_{t+1} (in) and lambda_t (out) per natural slot,
 // passed as kernel parameters (as the state's Slots are), so that each of a
@@ -140,23 +168,30 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z + g.z0;
   const bool live = x < g.nx && y < g.ny;
+  __shared__ float lsm[kPop][kAdjThreads];
   double abar_site = 0.0;
   if (live) {
     const int site = (z * g.ny + y) * g.nx + x;
     const Nbr nb = make_nbr(x, y, z, g);
 
-    // ---- gather dL/df* (streaming transpose: from x + c_q), issued after the
-    // forward recompute
-    float lf[kQ], lg[3][kM];
-    auto gather = [&]() {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    auto lgv = [&](int b, int i) { return lds(&lsm[kQ + kM * b + i][tid]); };
+    auto issue_gather = [&]() {
+      // ---- gather dL/df* (streaming transpose: from x + c_q) as asynchronous
+      // copies into shared memory, in flight during the forward recompute
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) lf[i] = L.in[i][site + nb(cx27(i), cy27(i), cz27(i))];
+      for (int i = 0; i < kQ; ++i) cp_async4(&lsm[i][tid], L.in[i] + site + nb(cx27(i), cy27(i), cz27(i)));
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int i = 0; i < kM; ++i)
-          lg[b][i] = L.in[mslot(b, i)][site + nb(mx7(i), my7(i), mz7(i))];
+          cp_async4(&lsm[kQ + kM * b + i][tid], L.in[mslot(b, i)] + site + nb(mx7(i), my7(i), mz7(i)));
+      cp_async_commit();
     };
+    // 16-bit storage: the state loads first; FP32: the lambda copies first
+    // (each measured faster)
+    constexpr bool kStateFirst = sizeof(T) == 2;
+    if (!kStateFirst) issue_gather();
 
     // ---- forward recompute (deviation variables, as in the step kernel)
     float sf[kQ];
@@ -171,6 +206,7 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
 #pragma unroll
       for (int i = 0; i < kM; ++i)
         sg[b][i] = Codec<T>::dec(P.p[mslot(b, ODD ? opp7(i) : i)][site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i))]);
+    if (kStateFirst) issue_gather();
     // sums of 216 w_i f_i times 1, c_a and c_a c_b, by 1-D passes with (1, 4, 1)
     float drho, jv[3], pv[3][3];
     {
@@ -253,19 +289,22 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
         for (int b = a; b < 3; ++b) D[a][b] = r * (a == b ? S[a][b] - tr3 : S[a][b]);
     }
 
-    gather();
+    cp_async_wait_all();
 
     // ---- magnetic collision
     const float omB = k.omegaB;
     float Bb[3], Vb[3], Q[3][3];  // Q[a][b] = sum_i mu_bi xi_ia
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      float m0 = 0.25f * lg[b][0];
+      float l[kM];
 #pragma unroll
-      for (int i = 1; i < kM; ++i) m0 += 0.125f * lg[b][i];
+      for (int i = 0; i < kM; ++i) l[i] = lgv(b, i);
+      float m0 = 0.25f * l[0];
+#pragma unroll
+      for (int i = 1; i < kM; ++i) m0 += 0.125f * l[i];
       Bb[b] = omB * m0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) Q[a][b] = omB * 0.125f * (lg[b][2 * a + 1] - lg[b][2 * a + 2]);
+      for (int a = 0; a < 3; ++a) Q[a][b] = omB * 0.125f * (l[2 * a + 1] - l[2 * a + 2]);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -330,7 +369,7 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
     {
       float tl[3][3][3];
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) tl[cz27(i) + 1][cy27(i) + 1][cx27(i) + 1] = lf[i];
+      for (int i = 0; i < kQ; ++i) tl[cz27(i) + 1][cy27(i) + 1][cx27(i) + 1] = lds(&lsm[i][tid]);
       const Fv Px{ax.psi}, Py{ay.psi}, Pz{az.psi}, DPx{ax.dpsi}, DPy{ay.dpsi}, DPz{az.dpsi};
       const Fv F0x{ax.F0}, F0y{ay.F0}, F0z{az.F0}, F1x{ax.F1}, F1y{ay.F1}, F1z{az.F1};
       const Fc<kFnF2> F2c;
@@ -474,7 +513,7 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int i = 0; i < kM; ++i) {
-        float v = (1.f - omB) * lg[b][i] + Bb[b];
+        float v = (1.f - omB) * lgv(b, i) + Bb[b];
         if (i > 0) {
           const int a = (i - 1) >> 1;
           v += (i & 1) ? Lb[a][b] : -Lb[a][b];
@@ -484,7 +523,8 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
     abar_site = (double)abar;
   }
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  block_sum_to(abar_site, partials + blk);
+  const int warp = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
+  warp_sum_to(abar_site, partials + blk * ((blockDim.x * blockDim.y) >> 5) + warp);
 }
 
 // ---------------------------------------------------------------------------
@@ -622,6 +662,23 @@ __global__ void init_adjoint_stencil_kernel(Grid g, const double* __restrict__ u
   }
 }
 
+// Deterministic two-level sum of n partials: kSumBlocks blocks sum fixed
+// chunks into stage[], then one block sums the stage.
+constexpr int kSumBlocks = 256;
+__global__ void sum_chunks_kernel(const double* __restrict__ partials, long long n, double* __restrict__ stage) {
+  __shared__ double sh[256];
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = per * blockIdx.x, hi = lo + per < n ? lo + per : n;
+  double a = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) a += partials[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) stage[blockIdx.x] = sh[0];
+}
 __global__ void sum_partials_kernel(const double* __restrict__ partials, long long n, double* __restrict__ out) {
   __shared__ double sh[256];
   double a = 0.0;
@@ -633,6 +690,11 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, long lo
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = sh[0];
+}
+// Sum of n partials (the buffer holds n + kSumBlocks doubles) into *out.
+inline void sum_partials(double* partials, long long n, double* out, cudaStream_t s) {
+  sum_chunks_kernel<<<kSumBlocks, 256, 0, s>>>(partials, n, partials + n);
+  sum_partials_kernel<<<1, 256, 0, s>>>(partials + n, kSumBlocks, out);
 }
 
 template <class T>
@@ -649,7 +711,7 @@ cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, con
     adjoint_step_kernel<T, true><<<gr, b, 0, s>>>(P, g, k, L, partials);
   else
     adjoint_step_kernel<T, false><<<gr, b, 0, s>>>(P, g, k, L, partials);
-  sum_partials_kernel<<<1, 256, 0, s>>>(partials, nblk, ddi);
+  sum_partials(partials, nblk * ((b.x * b.y) >> 5), ddi, s);
   return cudaGetLastError();
 }
 
@@ -658,8 +720,8 @@ cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, con
 long long adjoint_partials_needed(Grid g) {
   const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
   const dim3 bi = site_block(g, 128), gi = site_grid(g, bi);
-  const long long a = (long long)gr.x * gr.y * gr.z, c = (long long)gi.x * gi.y * gi.z;
-  return a > c ? a : c;
+  const long long a = (long long)gr.x * gr.y * gr.z * ((b.x * b.y) >> 5), c = (long long)gi.x * gi.y * gi.z;
+  return (a > c ? a : c) + kSumBlocks;
 }
 
 cudaError_t launch_step_adjoint(int storage, int odd, const void* pop, Grid g, const StepConsts& k, const float* lin,
@@ -685,7 +747,7 @@ cudaError_t launch_init_adjoint(Grid g, const StepConsts& k, const double* u, co
   double* dBb = ws + 15 * n3;
   init_adjoint_local_kernel<<<gr, b, 0, s>>>(g, k, u, B, lam, ubl, Bbl, dub, dBb, partials);
   init_adjoint_stencil_kernel<<<gr, b, 0, s>>>(g, ubl, Bbl, dub, dBb, ubar, Bbar);
-  sum_partials_kernel<<<1, 256, 0, s>>>(partials, (long long)gr.x * gr.y * gr.z, ddi);
+  sum_partials(partials, (long long)gr.x * gr.y * gr.z, ddi, s);
   return cudaGetLastError();
 }
 

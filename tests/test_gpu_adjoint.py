@@ -29,13 +29,43 @@ def _vjp_reference(pop, lam, tau_nu, tau_eta, di):
     return gx.numpy(), float(gd)
 
 
-@pytest.mark.parametrize("storage,nsteps", [("fp32", 3), ("fp32", 4), ("fp16", 3)])
-def test_step_adjoint_matches_autograd(storage, nsteps):
+def _di_terms(pop, lam, tau_nu, tau_eta, di):
+    """The per-site terms of dL/dd_i (their sum is the reference's gradient):
+    the site collision of the torch restatement with one d_i per site, built
+    from its own helpers, then streamed as in its step."""
+    shape = pop.shape[1:]
+    x = torch.tensor(pop).reshape(48, -1).T
+    d = torch.full((x.shape[0],), float(di), dtype=torch.float64, requires_grad=True)
+    omega, omegaB = 1.0 / tau_nu, 1.0 / tau_eta
+    f, g = x[:, :27], x[:, 27:].reshape(-1, 3, 7)
+    rho = f.sum(-1)
+    U = (f @ R.C27) / rho[:, None]
+    B = g.sum(-1)
+    J = R.current(torch.einsum("ia,sbi->sab", R.XI7, g), U, B, omegaB, d)
+    V = U - d[:, None] * J
+    L0 = V[:, :, None] * B[:, None, :] - B[:, :, None] * V[:, None, :]
+    geq = R.W7[None, None, :] * (B[:, :, None] + torch.einsum("ia,sab->sbi", R.XI7, L0) / R.CC2)
+    gs = g - omegaB * (g - geq)
+    fs = R.collide_fluid(f, R.feq(rho, U) + R.lorentz(B), U, omega)
+    post = torch.cat([fs, gs.reshape(-1, 21)], dim=-1).T.reshape((48,) + tuple(shape))
+    vel = R._velocities()
+    y = torch.stack([torch.roll(post[q], shifts=(int(vel[q, 2]), int(vel[q, 1]), int(vel[q, 0])), dims=(0, 1, 2))
+                     for q in range(48)])
+    (a,) = torch.autograd.grad((y * torch.tensor(lam)).sum(), [d])
+    return a.numpy()
+
+
+@pytest.mark.parametrize("storage,nsteps,shape", [("fp32", 3, (6, 5, 7)), ("fp32", 4, (6, 5, 7)),
+                                                 ("fp16", 3, (6, 5, 7)), ("fp32", 3, (5, 1, 20)),
+                                                 ("fp16", 4, (8, 20, 70)), ("bf16", 3, (4, 9, 130))])
+def test_step_adjoint_matches_autograd(storage, nsteps, shape):
     """One adjoint step at a state with either AA parity (3 or 4 forward steps),
-    vs torch autograd of the FP64 step at the GPU's own decoded state."""
+    vs torch autograd of the FP64 step at the GPU's own decoded state.  The
+    shapes cover blocks of one and of two warps (a one-plane y extent), rows
+    longer than a block with a ragged end, and more d_i partials than the
+    first summing level has blocks."""
     from paper_2212_11024_gb300 import Flame
     from paper_2212_11024_gb300.flame import library
-    shape = (6, 5, 7)
     nz, ny, nx = shape
     u, B = turbulence(shape, 13, 0.05)
     B[2] += 0.05
@@ -55,9 +85,15 @@ def test_step_adjoint_matches_autograd(storage, nsteps):
     torch.cuda.synchronize()
     got = lout.cpu().numpy().reshape((48,) + shape)
     ref, ref_d = _vjp_reference(pop, lam, 0.57, 0.62, 1.3)
+    terms = _di_terms(pop, lam, 0.57, 0.62, 1.3)
     sim.close()
     assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
-    assert abs(float(ddi[0]) - ref_d) < 1e-5 * abs(ref_d)
+    assert abs(terms.sum() - ref_d) < 1e-12 * np.abs(terms).sum()
+    # d_i: the sites' terms cancel (a random lambda; sum |a| / |sum a| up to
+    # ~5e3 here), so the bound is the FP32 rounding of each term, ~50 eps
+    # per term added as independent errors, plus 1e-5 of the total.
+    tol = 1e-5 * abs(ref_d) + 3e-6 * np.sqrt((terms ** 2).sum())
+    assert abs(float(ddi[0]) - ref_d) < tol
 
 
 def test_init_adjoint_matches_autograd():
