@@ -162,6 +162,17 @@ size_t flame_state_bytes(const flame_params *p);
  * FLAME_ERR_CUDA if the current device cannot be queried. */
 flame_status flame_create(flame_ctx **out, const flame_params *p, void *d_state, void *stream);
 
+/* Create a context without a population state, for the field-level
+ * diagnostics of a whole periodic lattice whose u and B the caller holds --
+ * a lattice split into z-slabs, whose slab contexts refuse the FFT
+ * diagnostics: flame_spectra_fields, flame_energy_budget and
+ * flame_band_energy with given fields (they use the parameters' tau_nu,
+ * tau_eta and d_i).  Every call that needs a state (flame_init,
+ * flame_step, flame_moments, flame_spectra, flame_set_state, ...) returns
+ * FLAME_ERR_STATE.  Errors: as flame_create, and FLAME_ERR_PARAM for a slab
+ * (halo_z = 1). */
+flame_status flame_create_fields(flame_ctx **out, const flame_params *p, void *stream);
+
 /* Fill the state with the populations of the initial fields (time t = 0):
  * f = f^mhd(0)(rho, u, B) (Sec. 3.1.1: 6th-order Hermite equilibrium plus
  * the Lorentz stress term) and g = g^Hall(0)(u, B, J0) (eq. gHall_eq) with
@@ -304,6 +315,14 @@ flame_status flame_halo_exchange(flame_ctx *lower, flame_ctx *upper);
  * FFTs by cuFFT (FP64), shell sums in FP64.  Either output may be NULL.
  * Synchronises. */
 flame_status flame_spectra(flame_ctx *ctx, int nshell, double *h_Eu, double *h_Eb);
+
+/* flame_spectra of given FP64 fields d_u and d_B ([3][N3] each, device,
+ * both required: FLAME_ERR_PARAM otherwise) instead of the state's u and B.
+ * As there, the m = 0 mode of B (its mean) is left out, so h_Eb is the
+ * spectrum of B - <B>.  Works on every non-slab context, including one from
+ * flame_create_fields.  Synchronises. */
+flame_status flame_spectra_fields(flame_ctx *ctx, int nshell, const double *d_u, const double *d_B, double *h_Eu,
+                                  double *h_Eb);
 
 /* Magnetic energy in a band of shells (the spectra of Sec. 4.4) and its
  * gradient, the loss of the differentiable runs:

@@ -198,12 +198,8 @@ size_t flame_state_bytes(const flame_params* p) {
          elem_bytes(p->storage);
 }
 
-flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state, void* stream) {
-  if (!out) return FLAME_ERR_PARAM;
-  *out = nullptr;
-  flame_status st = check_params(p);
-  if (st != FLAME_OK) return st;
-  if (!d_state || (reinterpret_cast<uintptr_t>(d_state) & 255u) != 0) return FLAME_ERR_PARAM;
+// flame_create and flame_create_fields (d_state null: no population state).
+static flame_status create_ctx(flame_ctx** out, const flame_params* p, void* d_state, void* stream) {
   flame_ctx* c = new (std::nothrow) flame_ctx;
   if (!c) return FLAME_ERR_PARAM;
   std::memset(static_cast<void*>(c), 0, sizeof(*c));
@@ -222,7 +218,7 @@ flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state,
     delete c;
     return FLAME_ERR_CUDA;
   }
-  if (p->variant == FLAME_FD_CURRENT &&
+  if (d_state && p->variant == FLAME_FD_CURRENT &&
       cudaMalloc(&c->d_bfield, 3 * elem_bytes(p->storage) * (size_t)p->nx * p->ny * p->nz) != cudaSuccess) {
     cudaFree(c->d_flags);
     delete c;
@@ -243,12 +239,30 @@ flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state,
   // The graph of the first G steps after flame_init (parity 0) is captured
   // here, with the context, so that the first flame_step does not pay for
   // the capture; the parity-1 graph is captured on its first use.
-  if (p->graph_steps > 0 && capture_graph(c, 0) != cudaSuccess) {
+  if (d_state && p->graph_steps > 0 && capture_graph(c, 0) != cudaSuccess) {
     flame_destroy(c);
     return FLAME_ERR_CUDA;
   }
   *out = c;
   return FLAME_OK;
+}
+
+flame_status flame_create(flame_ctx** out, const flame_params* p, void* d_state, void* stream) {
+  if (!out) return FLAME_ERR_PARAM;
+  *out = nullptr;
+  flame_status st = check_params(p);
+  if (st != FLAME_OK) return st;
+  if (!d_state || (reinterpret_cast<uintptr_t>(d_state) & 255u) != 0) return FLAME_ERR_PARAM;
+  return create_ctx(out, p, d_state, stream);
+}
+
+flame_status flame_create_fields(flame_ctx** out, const flame_params* p, void* stream) {
+  if (!out) return FLAME_ERR_PARAM;
+  *out = nullptr;
+  flame_status st = check_params(p);
+  if (st != FLAME_OK) return st;
+  if (p->halo_z) return FLAME_ERR_PARAM;  // the field diagnostics take whole periodic lattices
+  return create_ctx(out, p, nullptr, stream);
 }
 
 }  // extern "C"
@@ -259,6 +273,7 @@ static flame_status init_from(flame_ctx* c, const F* d_rho, const F* d_u, const 
                               const F* d_gradB) {
   if (!c) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  if (!c->state) return FLAME_ERR_STATE;
   if (!d_u || !d_B) return FLAME_ERR_PARAM;
   // a fresh initial state clears a previous non-finite condition
   c->sticky = FLAME_OK;
@@ -501,12 +516,14 @@ flame_status flame_reduce(flame_ctx* c, double* h) {
   return r[FLAME_SUM_NONFINITE] > 0 ? FLAME_ERR_NONFINITE : FLAME_OK;
 }
 
-flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb) {
-  const Range range("flame_spectra");
+// Shell spectra of the state's u, B (d_u = d_B = null) or of given FP64
+// fields [3][N3] each.
+static flame_status spectra_of(flame_ctx* c, int nshell, const double* d_u, const double* d_B, double* h_Eu,
+                               double* h_Eb) {
   flame_status st = usable(c);
   if (st != FLAME_OK && st != FLAME_ERR_NONFINITE) return st;
   if (c->p.halo_z) return FLAME_ERR_PARAM;  // a slab holds only part of the spectrum's lattice
-  if (!c->initialized) return FLAME_ERR_STATE;
+  if (!d_u && !c->initialized) return FLAME_ERR_STATE;
   if (nshell < 1 || nshell > 4096) return FLAME_ERR_PARAM;  // shell histogram lives in shared memory
   cudaError_t e;
   const size_t n3 = (size_t)flame::fft_stride(c->g.n3);  // aligned stride between the six fields
@@ -542,8 +559,16 @@ flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb)
   if (cufftSetStream(c->plan, c->stream) != CUFFT_SUCCESS) return cuda_fail(c, cudaErrorUnknown);
   double* u = c->d_fields;
   double* B = c->d_fields + 3 * n3;
-  e = flame::launch_moments(c->p.storage, c->parity, c->state, c->g, c->k, nullptr, u, B, nullptr, c->stream,
-                            (long long)n3);
+  if (!d_u) {
+    e = flame::launch_moments(c->p.storage, c->parity, c->state, c->g, c->k, nullptr, u, B, nullptr, c->stream,
+                              (long long)n3);
+  } else {
+    // each component to its aligned place in the workspace (cuFFT input)
+    const size_t row = (size_t)c->g.n3 * sizeof(double);
+    e = cudaMemcpy2DAsync(u, n3 * sizeof(double), d_u, row, row, 3, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(B, n3 * sizeof(double), d_B, row, row, 3, cudaMemcpyDeviceToDevice, c->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_shells, 0, 2 * (size_t)nshell * sizeof(double), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   for (int f = 0; f < 6; ++f) {
@@ -569,6 +594,18 @@ flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb)
   return FLAME_OK;
 }
 
+flame_status flame_spectra(flame_ctx* c, int nshell, double* h_Eu, double* h_Eb) {
+  const Range range("flame_spectra");
+  return spectra_of(c, nshell, nullptr, nullptr, h_Eu, h_Eb);
+}
+
+flame_status flame_spectra_fields(flame_ctx* c, int nshell, const double* d_u, const double* d_B, double* h_Eu,
+                                  double* h_Eb) {
+  const Range range("flame_spectra_fields");
+  if (!c || !d_u || !d_B) return FLAME_ERR_PARAM;
+  return spectra_of(c, nshell, d_u, d_B, h_Eu, h_Eb);
+}
+
 flame_status flame_get_state(flame_ctx* c, void* d_dst, long long* step, int* parity) {
   if (!c || !d_dst) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
@@ -583,7 +620,7 @@ flame_status flame_get_state(flame_ctx* c, void* d_dst, long long* step, int* pa
 flame_status flame_set_state(flame_ctx* c, const void* d_src, long long step, int parity) {
   if (!c || !d_src) return FLAME_ERR_PARAM;
   if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
-  if ((parity != 0 && parity != 1) || step < 0) return FLAME_ERR_STATE;
+  if (!c->state || (parity != 0 && parity != 1) || step < 0) return FLAME_ERR_STATE;
   cudaError_t e = cudaMemcpyAsync(c->state, d_src, flame_state_bytes(&c->p), cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   e = cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream);

@@ -81,6 +81,7 @@ def _lib():
         sig = {
             "flame_state_bytes": (ctypes.c_size_t, [P(Params)]),
             "flame_create": (i, [P(vp), P(Params), vp, vp]),
+            "flame_create_fields": (i, [P(vp), P(Params), vp]),
             "flame_init": (i, [vp, vp, vp, vp, vp, vp]),
             "flame_step": (i, [vp, i]),
             "flame_sync": (i, [vp]),
@@ -89,6 +90,7 @@ def _lib():
             "flame_populations": (i, [vp, vp]),
             "flame_reduce": (i, [vp, P(d)]),
             "flame_spectra": (i, [vp, i, P(d), P(d)]),
+            "flame_spectra_fields": (i, [vp, i, vp, vp, P(d), P(d)]),
             "flame_get_state": (i, [vp, vp, P(ctypes.c_longlong), P(i)]),
             "flame_set_state": (i, [vp, vp, ctypes.c_longlong, i]),
             "flame_destroy": (None, [vp]),
@@ -209,7 +211,7 @@ class Flame:
 
     def __init__(self, nx, ny, nz, tau_nu, tau_eta, d_i, storage="fp32", rho0=1.0, B_ref=(0.0, 0.0, 0.0),
                  init_noneq=True, check_every=0, strict_cfl=False, device=None, stream=None, graph_steps=0,
-                 variant="flame", kernel="auto", halo_z=False):
+                 variant="flame", kernel="auto", halo_z=False, fields_only=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -228,10 +230,17 @@ class Flame:
             raise FlameError(FLAME_ERR_PARAM, "flame_state_bytes")
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-            self.state = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             ctx = ctypes.c_void_p()
-            _check(lib.flame_create(ctypes.byref(ctx), ctypes.byref(self.p), ctypes.c_void_p(self.state.data_ptr()),
-                                    ctypes.c_void_p(self.stream.cuda_stream)), "flame_create")
+            if fields_only:
+                # no population state: the field-level diagnostics of given u, B
+                self.state = None
+                _check(lib.flame_create_fields(ctypes.byref(ctx), ctypes.byref(self.p),
+                                               ctypes.c_void_p(self.stream.cuda_stream)), "flame_create_fields")
+            else:
+                self.state = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+                _check(lib.flame_create(ctypes.byref(ctx), ctypes.byref(self.p),
+                                        ctypes.c_void_p(self.state.data_ptr()),
+                                        ctypes.c_void_p(self.stream.cuda_stream)), "flame_create")
         self._ctx = ctx
         self._lib = lib
 
@@ -395,10 +404,20 @@ class Flame:
         _check(rc, "flame_reduce_static")
         return out
 
-    def spectra(self, nshell):
+    def spectra(self, nshell, u=None, B=None):
+        """flame_spectra: shell spectra (E_u, E_B) numpy FP64 [nshell] of the
+        current state, or (flame_spectra_fields) of the given FP64 fields u, B
+        [3,nz,ny,nx]."""
         Eu = (ctypes.c_double * nshell)()
         Eb = (ctypes.c_double * nshell)()
-        _check(self._lib.flame_spectra(self._ctx_or_raise(), int(nshell), Eu, Eb), "flame_spectra")
+        if u is None and B is None:
+            _check(self._lib.flame_spectra(self._ctx_or_raise(), int(nshell), Eu, Eb), "flame_spectra")
+        else:
+            uu, bb = self._dev(u, 3), self._dev(B, 3)
+            cur = self._before()
+            rc = self._lib.flame_spectra_fields(self._ctx_or_raise(), int(nshell), self._ptr(uu), self._ptr(bb), Eu, Eb)
+            self._after(cur)
+            _check(rc, "flame_spectra_fields")
         return np.array(Eu[:]), np.array(Eb[:])
 
     def band_energy(self, lo, hi, B=None, grad=False, adjoint_seed=False):
@@ -438,6 +457,8 @@ class Flame:
         _check(self._lib.flame_debug_stall_next_step(self._ctx_or_raise(), int(tries)), "flame_debug_stall_next_step")
 
     def get_state(self):
+        if self.state is None:
+            raise FlameError(FLAME_ERR_STATE, "flame_get_state (a context without state)")
         dst = self.torch.empty_like(self.state)
         step = ctypes.c_longlong()
         par = ctypes.c_int()
@@ -448,6 +469,8 @@ class Flame:
         return dst, int(step.value), int(par.value)
 
     def set_state(self, src, step, parity):
+        if self.state is None:
+            raise FlameError(FLAME_ERR_STATE, "flame_set_state (a context without state)")
         if src.numel() != self.state.numel() or src.dtype != self.state.dtype:
             raise ValueError("state blob does not match these parameters")
         src = src.contiguous()

@@ -16,7 +16,13 @@ cudaMemcpy2DAsync on one stream); ``exchange_distributed`` is the same
 exchange between one slab per process over torch.distributed point-to-point
 calls, for a slab per GPU.  The scalar diagnostics of a split lattice are the
 FP64 sums of every slab (flame_reduce_sums) added -- an all-reduce across
-processes -- and combined by flame_reduce_combine.
+processes -- and combined by flame_reduce_combine.  The FFT
+diagnostics (spectra, the energy budget, a band energy) need the whole
+lattice: the slabs' u and B are assembled (gathered to one process, for a
+slab per GPU) and evaluated by a context without state over the whole
+lattice (flame_create_fields, flame_spectra_fields and the field forms of
+flame_energy_budget and flame_band_energy).  The gathered FP64 u and B take
+48 B per site, half the FP16 state of the same lattice.
 """
 from __future__ import annotations
 
@@ -60,6 +66,8 @@ class SlabGroup:
         stream = torch.cuda.current_stream(dev)
         self.slabs = [Flame(nx, ny, n, tau_nu, tau_eta, d_i, storage=storage, device=dev, stream=stream,
                             halo_z=True, **kw) for n in self.nzs]
+        self._whole = (int(nx), int(ny), int(nz), tau_nu, tau_eta, d_i, storage, dev, stream, kw)
+        self._fields = None
 
     def init(self, rho, u, B):
         """Initial fields [.., nz, ny, nx] of the whole lattice: each slab gets its
@@ -96,6 +104,36 @@ class SlabGroup:
         import torch
         return torch.cat([s.populations() for s in self.slabs], dim=-3)
 
+    def field_context(self):
+        """The context without state over the whole lattice (created on first
+        use) that evaluates the FFT diagnostics of the assembled fields."""
+        if self._fields is None:
+            nx, ny, nz, tau_nu, tau_eta, d_i, storage, dev, stream, kw = self._whole
+            self._fields = Flame(nx, ny, nz, tau_nu, tau_eta, d_i, storage=storage, device=dev, stream=stream,
+                                 fields_only=True, **kw)
+        return self._fields
+
+    def fields(self):
+        """u and B of the whole lattice, FP64 CUDA [3, nz, ny, nx]."""
+        m = self.moments()
+        return m["u"], m["B"]
+
+    def spectra(self, nshell):
+        """Shell spectra (E_u, E_B) of the whole lattice (flame_spectra_fields)."""
+        u, B = self.fields()
+        return self.field_context().spectra(nshell, u, B)
+
+    def energy_budget(self, nshell):
+        """(E, S, D) of the whole lattice (flame_energy_budget of its fields)."""
+        u, B = self.fields()
+        return self.field_context().energy_budget(nshell, u, B)
+
+    def band_energy(self, lo, hi, grad=False):
+        """flame_band_energy of the whole lattice's B: (L, dL/dB or None)."""
+        _, B = self.fields()
+        L, g, _ = self.field_context().band_energy(lo, hi, B, grad=grad)
+        return L, g
+
     def reduce(self):
         """FP64 scalars of the whole lattice from the slabs' raw sums."""
         sums = [s.reduce_sums() for s in self.slabs]
@@ -106,6 +144,9 @@ class SlabGroup:
     def close(self):
         for s in self.slabs:
             s.close()
+        if self._fields is not None:
+            self._fields.close()
+            self._fields = None
 
 
 def _run_view(state, p, run, elem_bytes):
@@ -162,3 +203,41 @@ def allreduce_sums(sums, dist):
     dist.all_reduce(m, op=dist.ReduceOp.MAX)
     t[SUM_UMAX] = m[0]
     return t.numpy()
+
+
+def gather_fields(fields, nzs, dist, rank, world, root=0):
+    """The whole lattice's field on `root` from every process's slab field
+    [..., nzs[rank], ny, nx] (slab r + 1 above slab r): the slabs in order,
+    concatenated along z, on root; None on the other ranks.  Point-to-point
+    (send / recv), so slabs of different plane counts need no padding."""
+    import torch
+    f = fields.contiguous()
+    if world == 1:
+        return f
+    if rank != root:
+        dist.send(f, root)
+        return None
+    parts = []
+    for r in range(world):
+        if r == root:
+            parts.append(f)
+            continue
+        buf = f.new_empty(tuple(f.shape[:-3]) + (int(nzs[r]),) + tuple(f.shape[-2:]))
+        dist.recv(buf, r)
+        parts.append(buf)
+    return torch.cat(parts, dim=-3)
+
+
+def diagnostics_distributed(compute, u, B, nzs, dist, rank, world, root=0):
+    """Evaluate a whole-lattice diagnostic of a lattice split into one slab
+    per process: the slabs' u and B [3, nzs[rank], ny, nx] are gathered to
+    `root` (gather_fields), compute(u, B) runs there -- for instance the
+    spectra of a context without state, ``lambda u, B: ctx.spectra(n, u, B)``
+    -- and its result (numpy arrays or numbers) is broadcast to every rank,
+    which all return it."""
+    uw = gather_fields(u, nzs, dist, rank, world, root)
+    Bw = gather_fields(B, nzs, dist, rank, world, root)
+    out = [compute(uw, Bw) if rank == root else None]
+    if world > 1:
+        dist.broadcast_object_list(out, src=root)
+    return out[0]

@@ -92,6 +92,13 @@ def test_flame_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert L.flame_create(ctypes.byref(ctx), ctypes.byref(bad), ctypes.c_void_p(0x1000), None) == F.FLAME_ERR_PARAM
     assert L.flame_step(None, 1) == F.FLAME_ERR_PARAM
     assert L.flame_sync(None) == F.FLAME_ERR_PARAM
+    # the context without state: the same parameter checks, and no slab
+    assert L.flame_create_fields(ctypes.byref(ctx), ctypes.byref(bad), None) == F.FLAME_ERR_PARAM
+    assert ctx.value is None
+    slab = F.make_params(4, 4, 4, 0.6, 0.6, 0.0, halo_z=True)
+    assert L.flame_create_fields(ctypes.byref(ctx), ctypes.byref(slab), None) == F.FLAME_ERR_PARAM
+    assert L.flame_create_fields(None, ctypes.byref(p), None) == F.FLAME_ERR_PARAM
+    assert L.flame_spectra_fields(None, 4, None, None, None, None) == F.FLAME_ERR_PARAM
 
 
 def test_units_match_table2_cfl():

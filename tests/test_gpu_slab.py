@@ -112,6 +112,72 @@ def test_slabs_match_the_oracle():
     assert rel_dev_err(fg, fo, rest, slice(27, 48)) < 1e-6
 
 
+def test_slab_fft_diagnostics_equal_one_context():
+    """Spectra, the energy budget and a band energy of the split lattice (the
+    slabs' u and B assembled and evaluated by a context without state)
+    against the single context's own (its state's u and B): the same FP64
+    fields through the same FFT code."""
+    shape = (9, 6, 16)
+    u, B = _fields(shape, 71)
+    one, grp = _pair(shape, 3, "fp16")
+    one.init(None, u, B)
+    grp.init(None, u, B)
+    one.step(5)
+    grp.step(5)
+    Eu1, Eb1 = one.spectra(9)
+    Eu2, Eb2 = grp.spectra(9)
+    assert np.allclose(Eu1, Eu2, rtol=1e-12, atol=0) and np.allclose(Eb1, Eb2, rtol=1e-12, atol=0)
+    assert Eb1[0] == 0.0 and Eb1[1] > 0.0  # the mean field is left out
+    for a, b in zip(one.energy_budget(9), grp.energy_budget(9)):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-13 * np.abs(a).max())
+    L1, g1, _ = one.band_energy(1, 3, grad=True)
+    L2, g2 = grp.band_energy(1, 3, grad=True)
+    assert abs(L1 - L2) <= 1e-12 * L1
+    assert torch.allclose(g1, g2, rtol=0, atol=1e-12 * float(g1.abs().max()))
+    # the field form on an ordinary context equals its state form
+    m = one.moments()
+    Eu3, Eb3 = one.spectra(9, m["u"], m["B"])
+    assert np.allclose(Eu1, Eu3, rtol=1e-12, atol=0) and np.allclose(Eb1, Eb3, rtol=1e-12, atol=0)
+    one.close()
+    grp.close()
+
+
+def test_context_without_state():
+    """flame_create_fields: the field diagnostics work, everything that needs
+    a state answers FLAME_ERR_STATE, and a slab is refused."""
+    from paper_2212_11024_gb300 import Flame, FlameError
+    from paper_2212_11024_gb300.flame import FLAME_ERR_PARAM, FLAME_ERR_STATE, library, make_params
+    shape = (4, 6, 8)
+    nz, ny, nx = shape
+    u, B = _fields(shape, 73)
+    f = Flame(nx, ny, nz, 0.6, 0.6, 1.0, fields_only=True)
+    lib = library()
+    for call in (lambda: f.init(None, u, B), lambda: f.step(1), lambda: f.moments(), lambda: f.spectra(4),
+                 lambda: f.energy_budget(4), lambda: f.band_energy(1, 2), lambda: f.get_state(),
+                 lambda: f.reduce()):
+        with pytest.raises(FlameError) as e:
+            call()
+        assert e.value.status == FLAME_ERR_STATE
+    blob = torch.zeros(48 * nx * ny * nz * 4, dtype=torch.uint8, device="cuda")
+    assert lib.flame_set_state(f._ctx, ctypes.c_void_p(blob.data_ptr()), 0, 0) == FLAME_ERR_STATE
+    ut = torch.tensor(u, device="cuda")
+    Bt = torch.tensor(B, device="cuda")
+    from oracle import spectra as S
+    Eu, Eb = f.spectra(5, ut, Bt)
+    Eu_o = S.shell_spectrum(u, 5)
+    Bm = B - B.reshape(3, -1).mean(1)[:, None, None, None]
+    Eb_o = S.shell_spectrum(Bm, 5)
+    assert np.allclose(Eu, Eu_o, rtol=1e-12, atol=1e-18) and np.allclose(Eb, Eb_o, rtol=1e-12, atol=1e-18)
+    E, _, _ = f.energy_budget(5, ut, Bt)
+    # the budget's E(n) keeps B's mean mode (shell 0)
+    Eb_full = S.shell_spectrum(B, 5)
+    assert np.allclose(E, Eu_o + Eb_full, rtol=1e-12, atol=1e-18)
+    f.close()
+    ctx = ctypes.c_void_p()
+    p = make_params(nx, ny, nz, 0.6, 0.6, 1.0, halo_z=True)
+    assert lib.flame_create_fields(ctypes.byref(ctx), ctypes.byref(p), None) == FLAME_ERR_PARAM
+
+
 def test_slab_contexts_refuse_what_they_cannot_do():
     from paper_2212_11024_gb300 import Flame, FlameError
     from paper_2212_11024_gb300.flame import FLAME_ERR_PARAM, FLAME_ERR_STATE, library

@@ -161,6 +161,45 @@ def test_slab_exchange_matches_the_whole_lattice(world, shape, port):
     assert all(red for _, red in res), res
 
 
+def _gather_worker(rank, world, port, shape, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import spectra as S
+        from paper_2212_11024_gb300 import slab as SL
+        nz = shape[0]
+        rng = np.random.default_rng(17)
+        u = rng.standard_normal((3,) + shape)
+        B = rng.standard_normal((3,) + shape) + 0.1
+        z0s, nzs = SL.split(nz, world)
+        z0, n = z0s[rank], nzs[rank]
+        us = torch.from_numpy(u[:, z0:z0 + n].copy())
+        Bs = torch.from_numpy(B[:, z0:z0 + n].copy())
+        root = world - 1
+        g = SL.gather_fields(us, nzs, dist, rank, world, root=root)
+        gather_ok = (g is None) if rank != root else np.array_equal(g.numpy(), u)
+        spec = SL.diagnostics_distributed(
+            lambda uw, Bw: (S.shell_spectrum(uw.numpy(), 6), S.shell_spectrum(Bw.numpy(), 6)),
+            us, Bs, nzs, dist, rank, world, root=root)
+        spec_ok = np.array_equal(spec[0], S.shell_spectrum(u, 6)) and np.array_equal(spec[1], S.shell_spectrum(B, 6))
+        out[rank] = (gather_ok, spec_ok)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,shape,port", [(1, (4, 3, 5), 29521), (2, (5, 4, 6), 29522), (3, (7, 3, 4), 29523)])
+def test_fft_diagnostics_of_a_split_lattice(world, shape, port):
+    """The slabs' fields gathered to one rank (slabs of unequal plane
+    counts) equal the whole lattice's, and a diagnostic evaluated there
+    reaches every rank unchanged."""
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    mp.start_processes(_gather_worker, args=(world, port, shape, out), nprocs=world, join=True, start_method="spawn")
+    res = [out[r] for r in range(world)]
+    assert all(a and b for a, b in res), res
+
+
 def test_halo_plan_runs():
     """The runs of the plan: 9 fluid + 3 magnetic slots per face, the
     populations moving across the face (c_z = -1 slots 0..8 and 45..47,
