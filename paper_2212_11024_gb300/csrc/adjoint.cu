@@ -26,6 +26,8 @@
 //   U = j/rho: jbar = Ubar/rho, rhobar -= Ubar.U/rho;
 //   moments: fbar_i = rhobar + jbar.c_i + Pibar : c_i c_i,
 //            gbar_bi += Bbar_b + sum_a xi_ia Lambdabar_ab.
+#include <type_traits>
+
 #include "aa.cuh"
 
 namespace flame {
@@ -35,7 +37,8 @@ namespace {
 // goes into shared memory by asynchronous copies (cp.async) that are in
 // flight during the forward recompute, and lambda is read from there where
 // it is used rather than held in registers; for 16-bit storage the state
-// loads are issued before the copies, for FP32 after them.  The d_i
+// loads are issued before the copies, for FP32 after them; both carry a
+// 256-byte L2 prefetch hint.  The d_i
 // contributions are summed per warp in FP64 (no block barrier) and the
 // partials added in a fixed order by two small kernels.  Timed at
 // 256^3 (GLUPS FP32 / FP16 storage): one 256-thread block of 185 registers
@@ -45,7 +48,10 @@ namespace {
 // read from shared memory where used, 128 x 5, 9.71 / 10.39 (128 x 6, 80
 // registers with spills: 9.26 / 9.85); the partials summed by one block had
 // cost ~5 %: 10.23 / 10.91 with the two-level sum, 10.27 / 11.0 with the
-// per-storage load order and 64 x 10.  (Per-warp sums in FP32 gained 0.7 %
+// per-storage load order and 64 x 10, 10.51 / 11.16 with read-only state
+// loads and 256-byte L2 prefetch hints on them and on the lambda copies
+// (10.46 / 11.06 for the state loads alone; f32x2 pairs inside the 1-D
+// passes: 10.35 / 11.04, not kept).  (Per-warp sums in FP32 gained 0.7 %
 // but, where the sites' terms cancel -- a random lambda: sum |a| / |sum a|
 // ~ 5000 -- they added ~5x the rounding of the per-site arithmetic to d_i.)
 constexpr int kAdjThreads = 64;
@@ -142,7 +148,7 @@ __device__ __forceinline__ void block_sum_to(double v, double* out) {
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.ca.shared.global.L2::256B [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ float lds(const float* p) {
   float v;
@@ -151,6 +157,22 @@ __device__ __forceinline__ float lds(const float* p) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Read-only state loads with an L2 prefetch-size hint (the neighbouring
+// warps' segments of the same rows arrive with the first request).
+template <class T>
+__device__ __forceinline__ float ld_state(const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    float v;
+    asm volatile("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+  } else {
+    unsigned short h;
+    asm volatile("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(h) : "l"(p));
+    if constexpr (std::is_same_v<T, __half>) return __half2float(__ushort_as_half(h));
+    else return __bfloat162float(__ushort_as_bfloat16(h));
+  }
+}
 
 // Base pointers of lambda_{t+1} (in) and lambda_t (out) per natural slot,
 // passed as kernel parameters (as the state's Slots are), so that each of a
@@ -198,14 +220,14 @@ __global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       const int slot = ODD ? opp27(i) : i;
-      sf[i] = Codec<T>::dec(P.p[slot][site + src_off<ODD>(nb, cx27(i), cy27(i), cz27(i))]);
+      sf[i] = ld_state<T>(P.p[slot] + site + src_off<ODD>(nb, cx27(i), cy27(i), cz27(i)));
     }
     float sg[3][kM];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int i = 0; i < kM; ++i)
-        sg[b][i] = Codec<T>::dec(P.p[mslot(b, ODD ? opp7(i) : i)][site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i))]);
+        sg[b][i] = ld_state<T>(P.p[mslot(b, ODD ? opp7(i) : i)] + site + src_off<ODD>(nb, mx7(i), my7(i), mz7(i)));
     if (kStateFirst) issue_gather();
     // sums of 216 w_i f_i times 1, c_a and c_a c_b, by 1-D passes with (1, 4, 1)
     float drho, jv[3], pv[3][3];
