@@ -18,6 +18,13 @@ timed steps (a run that went non-finite is still timed, but is flagged).
 ``--adjoint`` times flame_step_adjoint instead: one stored state, a seeded
 FP32 lambda_{t+1}, 576 B per update with FP32 storage (state read, lambda
 gathered and written), 480 with 16-bit storage.
+
+``--slabs K[,K...]`` times the lattice split into K z-slabs on one GPU
+(SlabGroup: every slab's step, then the AA halo exchange through every
+face, one launch per slab and step), against which the one-context lines
+show the decomposition's cost.
+
+    python -m paper_2212_11024_gb300.throughput --n 256 --slabs 1,2,4 --storage fp16
 """
 from __future__ import annotations
 
@@ -110,6 +117,41 @@ def adjoint_throughput(n, storage="fp32", steps=30, warmup=3, d_i=None, tau=0.51
                 glups=n ** 3 / (ms * 1e-3) / 1e9, bytes_per_update=bpu)
 
 
+def slab_throughput(n, nslabs, storage="fp16", steps=200, warmup=20, d_i=None, tau=0.51, fields=None,
+                    device=None):
+    """Time ``steps`` steps of the n^3 lattice split into ``nslabs`` z-slabs
+    (SlabGroup); returns a dict like step_throughput's, with the bytes the
+    halo exchange moves per step."""
+    import torch
+
+    from .slab import SlabGroup
+
+    if fields is None:
+        u, B = inputs.turbulence((n, n, n), 3, 4, 0.05, 0.05, shells=(1, 4))
+    else:
+        u, B = fields
+    d_i = 0.05 * n if d_i is None else d_i
+    grp = SlabGroup(n, n, n, nslabs, tau, tau, d_i, storage=storage, device=device)
+    try:
+        grp.init(None, u, B)
+        grp.step(warmup)
+        stream = grp.slabs[0].stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        grp.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        bad = int(grp.reduce()["nonfinite"])
+    finally:
+        grp.close()
+    # per face and step: 12 slot-planes each way
+    halo = 2 * 12 * n * n * (STATE_BYTES[storage] // 96) * nslabs
+    return dict(n=n, slabs=nslabs, storage=storage, steps=steps, ms_per_step=ms, glups=n ** 3 / (ms * 1e-3) / 1e9,
+                state_bytes_per_update=STATE_BYTES[storage], halo_bytes_per_step=halo, nonfinite_sites=bad)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--n", type=int, default=256)
@@ -124,8 +166,17 @@ def main(argv=None):
                     help="HBM bandwidth to report the state traffic against (GB/s)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time flame_step_adjoint (per storage) instead of the forward step")
+    ap.add_argument("--slabs", default=None, help="slab counts to time the z-slab decomposition with (e.g. 1,2,4)")
     a = ap.parse_args(argv)
     u, B = inputs.turbulence((a.n,) * 3, 3, 4, 0.05, 0.05, shells=(1, 4))
+    if a.slabs:
+        for st in a.storage.split(","):
+            for k in a.slabs.split(","):
+                r = slab_throughput(a.n, int(k), st, a.steps, a.warmup, a.d_i, a.tau, fields=(u, B))
+                if a.peak_gbs:
+                    r["frac_of_peak"] = r["glups"] * r["state_bytes_per_update"] / a.peak_gbs
+                print(json.dumps(r), flush=True)
+        return
     if a.adjoint:
         for st in a.storage.split(","):
             r = adjoint_throughput(a.n, st, min(a.steps, 100), a.warmup, a.d_i, a.tau, fields=(u, B))
