@@ -92,9 +92,12 @@ def parse_variant(spec):
 
 def kernel_name(storage, kernel, n):
     """The step kernel flame_step launches for this storage at n^3."""
-    if kernel == "auto" and storage in ("fp16", "bf16") and n % 64 == 0 and 64 <= n <= 1024:
-        if n in (576, 640):
-            return f"step_row_kernel<{storage}> (half x rows staged by bulk copies, packed FP32 pairs)"
+    row = (n % 64 == 0 if n <= 256 else n % 8 == 0) and 64 <= n <= 1024
+    if kernel == "auto" and storage in ("fp16", "bf16") and row:
+        if 512 < n <= 640:
+            if n % 16 == 0:
+                return f"step_row_kernel<{storage}> (half x rows staged by bulk copies, packed FP32 pairs)"
+            return f"step_kernel<{storage}> (one site per thread)"
         return f"step_row_kernel<{storage}> (staged x rows, packed FP32 pairs)"
     return f"step_kernel<{storage}> (one site per thread)"
 

@@ -49,31 +49,43 @@ cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 // Row lengths where the row kernel beats the one-site kernel, and with how
 // many segments per tile.  Timed with FP16 storage on ~4M-site lattices
 // (nx x m x m, GLUPS; whole rows / half rows / one-site): 256 31.9 / - /
-// 24.2, 320 29.2 / 20.6 / 21.2, 384 26.6 / 22.0 / 22.5, 448 27.6 / 21.9 /
-// 22.8, 512 30.7 / 27.5 / 24.4, 576 21.9 / 24.4 / 21.9, 640 24.2 / 26.7 /
-// 23.0, 704 25.0 / 20.9 / 23.2, 768 27.8 / 24.6 / 24.3, 832 24.6 / 22.2 /
-// 22.2, 896 26.3 / 23.7 / 22.9, 960 27.9 / 23.7 / 23.3, 1024 29.3 / 26.5 /
+// 24.2, 264 24.5 / - / 18.9, 320 29.2 / 20.6 / 21.2, 328 24.3 / - / 20.7,
+// 384 26.6 / 22.0 / 22.5, 400 26.7 / 21.8 / 22.0, 448 27.6 / 21.9 / 22.8,
+// 456 26.7 / - / 23.0, 504 28.5 / - / 24.1, 512 30.7 / 27.5 / 24.4, 520
+// 19.6 / - / 20.7, 528 20.1 / 22.5 / 20.9, 544 20.8 / 23.2 / 21.3, 552 20.8
+// / - / 21.3, 560 21.3 / 24.0 / 21.5, 568 21.3 / - / 21.7, 576 21.9 / 24.4
+// / 21.9, 640 24.2 / 26.7 / 23.0, 704 25.0 / 20.9 / 23.2, 744 26.6 / - /
+// 23.9, 768 27.8 / 24.6 / 24.3, 832 24.6 / 22.2 / 22.2, 896 26.3 / 23.7 /
+// 22.9, 960 27.9 / 23.7 / 23.3, 1000 28.1 / - / 22.7, 1024 29.3 / 26.5 /
 // 23.1 (384, 448 and 704-960 before the direct stores addressed their rows
 // from slot bases, which gained 5-8 % at 320-1024; 64-192 as in earlier
 // timings: 28.0 / 24.1, 31.8 / 24.2, 29.4 / 23.5 whole rows against
-// one-site).  Whole rows win everywhere but at 576 and 640 sites, where a
-// whole row's block of 288 / 320 threads with 96 KB or more of stages fits
-// once per SM; half rows per tile (three blocks per SM) are the faster
-// tiling there.  Elsewhere half rows lose: twice the copies per site (96 per
-// tile on odd steps, the halo across a row's end by a copy of its own) for
-// the same warps per SM.
-bool row_kernel_wins(int nx) { return true; }
+// one-site).  Whole rows win up to 512 sites and above 640.  Between, a
+// whole row's block of 260-320 threads (128 registers each) fits once per
+// SM; there half rows per tile (three blocks per SM) are the faster tiling
+// where a half row is a whole number of 16-byte units (nx a multiple of
+// 16), and the one-site kernel where it is not.  Elsewhere half rows lose:
+// twice the copies per site (96 per tile on odd steps, the halo across a
+// row's end by a copy of its own) for the same warps per SM.
+bool row_kernel_wins(int nx) { return !(nx > 512 && nx <= 640 && nx % 16 != 0); }
 
 // Segments per tile of the automatic choice (kernel = 0).
-int row_auto_segments(int nx) { return nx == 576 || nx == 640 ? 2 : 1; }
+int row_auto_segments(int nx) { return nx > 512 && nx <= 640 ? 2 : 1; }
+
+// Row lengths the row kernel stages: up to 256 sites by tensor-map boxes,
+// whose shared-memory destinations (the odd step's runs of three rows, 6 nx
+// bytes apart) must be 128-byte aligned, so nx a multiple of 64; longer rows
+// by bulk copies of whole rows, which need 16-byte units, so nx a multiple
+// of 8.
+static bool row_length_ok(int nx) { return nx <= kBoxMaxX ? nx % 64 == 0 : nx % 8 == 0; }
 
 bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel) {
   if (kernel == 1) return false;
   const bool base = variant >= kVarFlame && variant <= kVarFdCurrent && (storage == 2 || storage == 3) &&
-                    g.nx >= 64 && g.nx <= 2 * kRowMaxThreads && g.nx % 64 == 0 &&
+                    g.nx >= 64 && g.nx <= 2 * kRowMaxThreads && row_length_ok(g.nx) &&
                     (reinterpret_cast<uintptr_t>(pop) & 15u) == 0;
   if (!base) return false;
-  if (kernel == 3) return g.nx > kBoxMaxX;  // half rows: rows of more than 256 sites
+  if (kernel == 3) return g.nx > kBoxMaxX && g.nx % 16 == 0;  // half rows: whole 16-byte units per half
   if (kernel == 2) return true;
   return row_kernel_wins(g.nx);
 }

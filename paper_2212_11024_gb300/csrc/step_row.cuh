@@ -32,11 +32,15 @@
 // variant is instantiated in a translation unit of its own (step_row.cu,
 // step_row_bgk.cu, step_row_emhd.cu, step_row_fd.cu), so they compile in
 // parallel.
-// Requirements: 16-bit storage, 64 <= nx <= 1024 with nx a multiple of 64
-// (row copies of whole 16-byte units, a whole number of warps), a 16-byte
-// aligned state; flame_step uses it for the row lengths where it is faster
-// (row_kernel_wins).  Rows longer than 256 sites are moved by one bulk copy
-// per storage slot instead of tensor-map boxes.
+// Requirements: 16-bit storage, 64 <= nx <= 1024, a 16-byte aligned state.
+// Rows of up to 256 sites are staged by tensor-map boxes, whose shared-memory
+// destinations must be 128-byte aligned: the odd step's runs of three rows
+// start 6 nx bytes apart, so nx is a multiple of 64 there.  Longer rows are
+// moved by one bulk copy per storage slot (16-byte units: nx a multiple of
+// 8; half rows per tile: of 16).  Warp 0, which issues the copies, is always
+// whole (nx / 2 >= 32 threads); the last warp of a block may be partial.
+// flame_step uses the kernel for the row lengths where it is faster
+// (row_kernel_wins).
 #pragma once
 
 #include <cuda.h>
@@ -908,8 +912,10 @@ cudaError_t row_launch(const RowCall& c) {
 
 template <class T, bool ODD, int VAR>
 cudaError_t row_nx(const RowCall& c) {
+  // the alignment the staging copies need (see the requirements above)
+  if (c.g.nx <= kBoxMaxX ? c.g.nx % 64 != 0 : c.g.nx % 8 != 0) return cudaErrorInvalidValue;
   if (c.segments == 2) {
-    if (c.g.nx <= kBoxMaxX) return cudaErrorInvalidValue;
+    if (c.g.nx <= kBoxMaxX || c.g.nx % 16 != 0) return cudaErrorInvalidValue;
     return c.g.nx == 512 ? row_launch<T, ODD, 512, 2, VAR, 2>(c) : row_launch<T, ODD, 0, 2, VAR, 2>(c);
   }
   switch (c.g.nx) {

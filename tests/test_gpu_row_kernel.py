@@ -2,8 +2,8 @@
 two sites per thread in packed FP32 pairs) against the FP64 oracle and
 against the one-site kernel, for the paper's scheme and its variants (BGK
 fluid, electron MHD, finite-difference current).  Row lengths 64, 128, 256
-and 512 take the compile-time row length instantiations, 192, 960 and 1024
-the general one."""
+and 512 take the compile-time row length instantiations, 192, 328, 960, 1000
+and 1024 the general one (328 and 1000: blocks whose last warp is partial)."""
 import numpy as np
 import pytest
 
@@ -37,7 +37,8 @@ def _thin(shape):
 # one (192, and 960 / 1024 with 480- / 512-thread blocks); single-row and
 # single-plane lattices, where a row's periodic y / z neighbours are the row
 # itself
-SHAPES = [(6, 5, 64), (4, 3, 128), (3, 4, 192), (2, 3, 512), (1, 1, 64), (1, 2, 256), (2, 1, 960), (1, 2, 1024)]
+SHAPES = [(6, 5, 64), (4, 3, 128), (3, 4, 192), (2, 3, 512), (1, 1, 64), (1, 2, 256), (2, 1, 960), (1, 2, 1024),
+          (1, 2, 328), (2, 1, 1000)]
 B0 = np.array([0.0, 0.02, 0.05])
 
 
@@ -121,7 +122,7 @@ def test_row_kernel_graph_replay_is_bit_identical():
 # collision), 256 (three stages, in-place TMA stores), 512 and 960 (two
 # stages, direct stores; compile-time and general row length)
 @pytest.mark.parametrize("shape,storage", [((4, 3, 64), "fp16"), ((2, 3, 256), "bf16"), ((2, 3, 512), "fp16"),
-                                           ((2, 1, 960), "bf16")])
+                                           ((2, 1, 960), "bf16"), ((1, 2, 328), "fp16")])
 def test_wait_limit_on_every_pipeline(shape, storage, variant="flame"):
     """A stalled step (barriers armed, copies never issued, 256 polls) on
     each pipeline of the row kernel reports FLAME_ERR_TIMEOUT, leaves the
@@ -204,7 +205,7 @@ def test_row_kernel_wait_limit_reports_timeout():
 
 # the variants on compile-time (64, 256) and general (192, 960: bulk row
 # copies) row lengths, including a single-row lattice
-VARIANT_SHAPES = [(6, 5, 64), (3, 4, 192), (2, 3, 256), (2, 1, 960), (1, 1, 64)]
+VARIANT_SHAPES = [(6, 5, 64), (3, 4, 192), (2, 3, 256), (2, 1, 960), (1, 1, 64), (2, 1, 456)]
 
 
 def _variant_run(shape, storage, kernel, variant, steps, seed):
@@ -275,7 +276,8 @@ def test_row_kernel_variant_graph_replay_is_bit_identical(variant):
 # segment's halos replace the whole row's wrap-around, the results go
 # straight to HBM; the per-site arithmetic is the same, so the populations
 # must equal the whole-row tiling's bit for bit.
-HALF_SHAPES = [(2, 3, 320), (2, 2, 512), (1, 2, 576), (2, 1, 640), (1, 1, 960), (2, 1, 1024)]
+HALF_SHAPES = [(2, 3, 320), (2, 2, 512), (1, 2, 576), (2, 1, 640), (1, 1, 960), (2, 1, 1024), (1, 2, 400),
+               (2, 1, 528)]
 
 
 @pytest.mark.parametrize("shape", HALF_SHAPES)
@@ -315,7 +317,7 @@ def test_half_rows_equal_whole_rows_variants(variant):
         s.close()
 
 
-@pytest.mark.parametrize("shape", [(1, 2, 576), (2, 1, 640)])
+@pytest.mark.parametrize("shape", [(1, 2, 576), (2, 1, 640), (1, 2, 560)])
 def test_half_rows_vs_oracle(shape):
     """The row lengths where whole rows leave too few warps per SM, on half
     rows, against the oracle at the row kernel's FP16 bounds."""
@@ -350,3 +352,29 @@ def test_wait_limit_on_half_rows(shape):
     torch.cuda.synchronize()
     assert torch.equal(blob0, blob1) and st.value == 3
     sim.close()
+
+
+@pytest.mark.parametrize("nx,expect", [(456, "row"), (544, "row_half"), (552, "site"), (1000, "row")])
+def test_automatic_choice_between_the_tilings(nx, expect):
+    """kernel "auto" is the tiling timed fastest at each row length: whole
+    rows up to 512 sites and above 640, half rows between where nx is a
+    multiple of 16, the one-site kernel where it is not.  The tilings of the
+    row kernel agree bit for bit and differ from the one-site kernel, so
+    auto equals the expected kernel bit for bit and differs from the other
+    kind."""
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    shape = (2, 1, nx)
+    nz, ny, _ = shape
+    u, B = _fields(shape, 63)
+    other = "site" if expect != "site" else "row"
+    pops = {}
+    for k in ("auto", expect, other):
+        sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0), kernel=k)
+        sim.init(None, u, B)
+        sim.step(21)
+        pops[k] = sim.populations()
+        assert sim.sync() is None
+        sim.close()
+    assert torch.equal(pops["auto"], pops[expect])
+    assert not torch.equal(pops["auto"], pops[other])
