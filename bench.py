@@ -92,7 +92,7 @@ def parse_variant(spec):
 
 def kernel_name(storage, kernel, n):
     """The step kernel flame_step launches for this storage at n^3."""
-    row = (n % 64 == 0 if n <= 256 else n % 8 == 0) and 64 <= n <= 1024
+    row = n % 8 == 0 and 64 <= n <= 1024 and (n >= 96 or n == 64)
     if kernel == "auto" and storage in ("fp16", "bf16") and row:
         if 512 < n <= 640:
             if n % 16 == 0:

@@ -103,8 +103,8 @@ typedef struct {
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
     int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant), a 16-byte
-                         aligned state and nx a multiple of 64 up to 256 or of 8 from
-                         264 to 1024 use the row kernel (x rows staged in shared memory,
+                         aligned state and nx a multiple of 8 from 96 to 1024, or 64,
+                         use the row kernel (x rows staged in shared memory,
                          two sites per thread in packed FP32 pairs; half a row per tile
                          from 513 to 640 sites where nx is a multiple of 16, a whole row
                          below 513 and above 640: the faster tilings as timed), everything

@@ -46,9 +46,9 @@ cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConst
 
 // The step for 16-bit storage as a persistent kernel over x rows staged in
 // shared memory (step_row.cuh), two sites per thread in packed FP32 pairs:
-// every variant, 64 <= nx <= 1024 with nx a multiple of 64 up to 256 and of
-// 8 above (automatic choice: where the row kernel is the faster one), a
-// 16-byte aligned state; half rows for nx > 256 a multiple of 16 only.  flag bit 1: a
+// every variant, 64 <= nx <= 1024 with nx a multiple of 8 (automatic choice:
+// where the row kernel is the faster one), a 16-byte aligned state; half
+// rows for nx > 256 a multiple of 16 only.  flag bit 1: a
 // non-finite moment; bit 2: a staged copy did not complete within the wait
 // limit.
 bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel = 0);

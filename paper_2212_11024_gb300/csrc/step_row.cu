@@ -48,8 +48,10 @@ cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 
 // Row lengths where the row kernel beats the one-site kernel, and with how
 // many segments per tile.  Timed with FP16 storage on ~4M-site lattices
-// (nx x m x m, GLUPS; whole rows / half rows / one-site): 256 31.9 / - /
-// 24.2, 264 24.5 / - / 18.9, 320 29.2 / 20.6 / 21.2, 328 24.3 / - / 20.7,
+// (nx x m x m, GLUPS; whole rows / half rows / one-site): 72 18.6 / - /
+// 18.9, 96 24.5 / - / 23.5, 120 28.2 / - / 23.2, 136 21.3 / - / 20.5, 160
+// 25.2 / - / 22.6, 200 23.9 / - / 21.9, 224 26.4 / - / 23.3, 248 28.8 / - /
+// 23.6, 256 31.9 / - / 24.2, 264 24.5 / - / 18.9, 320 29.2 / 20.6 / 21.2, 328 24.3 / - / 20.7,
 // 384 26.6 / 22.0 / 22.5, 400 26.7 / 21.8 / 22.0, 448 27.6 / 21.9 / 22.8,
 // 456 26.7 / - / 23.0, 504 28.5 / - / 24.1, 512 30.7 / 27.5 / 24.4, 520
 // 19.6 / - / 20.7, 528 20.1 / 22.5 / 20.9, 544 20.8 / 23.2 / 21.3, 552 20.8
@@ -60,24 +62,26 @@ cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 // 23.1 (384, 448 and 704-960 before the direct stores addressed their rows
 // from slot bases, which gained 5-8 % at 320-1024; 64-192 as in earlier
 // timings: 28.0 / 24.1, 31.8 / 24.2, 29.4 / 23.5 whole rows against
-// one-site).  Whole rows win up to 512 sites and above 640.  Between, a
+// one-site).  Whole rows win from 96 sites (and at 64) up to 512 and above
+// 640; below 96 a block of under 48 threads carries a tile's copies for too
+// few sites and the one-site kernel is as fast.  Between 512 and 640, a
 // whole row's block of 260-320 threads (128 registers each) fits once per
 // SM; there half rows per tile (three blocks per SM) are the faster tiling
 // where a half row is a whole number of 16-byte units (nx a multiple of
 // 16), and the one-site kernel where it is not.  Elsewhere half rows lose:
 // twice the copies per site (96 per tile on odd steps, the halo across a
 // row's end by a copy of its own) for the same warps per SM.
-bool row_kernel_wins(int nx) { return !(nx > 512 && nx <= 640 && nx % 16 != 0); }
+bool row_kernel_wins(int nx) {
+  return !((nx > 512 && nx <= 640 && nx % 16 != 0) || (nx < 96 && nx % 64 != 0));
+}
 
 // Segments per tile of the automatic choice (kernel = 0).
 int row_auto_segments(int nx) { return nx > 512 && nx <= 640 ? 2 : 1; }
 
-// Row lengths the row kernel stages: up to 256 sites by tensor-map boxes,
-// whose shared-memory destinations (the odd step's runs of three rows, 6 nx
-// bytes apart) must be 128-byte aligned, so nx a multiple of 64; longer rows
-// by bulk copies of whole rows, which need 16-byte units, so nx a multiple
-// of 8.
-static bool row_length_ok(int nx) { return nx <= kBoxMaxX ? nx % 64 == 0 : nx % 8 == 0; }
+// Row lengths the row kernel stages: whole 16-byte units per row (up to 256
+// sites by tensor-map boxes of runs placed at 128-byte aligned offsets,
+// longer rows by bulk copies).
+static bool row_length_ok(int nx) { return nx % 8 == 0; }
 
 bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel) {
   if (kernel == 1) return false;

@@ -32,12 +32,12 @@
 // variant is instantiated in a translation unit of its own (step_row.cu,
 // step_row_bgk.cu, step_row_emhd.cu, step_row_fd.cu), so they compile in
 // parallel.
-// Requirements: 16-bit storage, 64 <= nx <= 1024, a 16-byte aligned state.
-// Rows of up to 256 sites are staged by tensor-map boxes, whose shared-memory
-// destinations must be 128-byte aligned: the odd step's runs of three rows
-// start 6 nx bytes apart, so nx is a multiple of 64 there.  Longer rows are
-// moved by one bulk copy per storage slot (16-byte units: nx a multiple of
-// 8; half rows per tile: of 16).  Warp 0, which issues the copies, is always
+// Requirements: 16-bit storage, 64 <= nx <= 1024 with nx a multiple of 8
+// (rows of whole 16-byte units; half rows per tile: of 16), a 16-byte
+// aligned state.  Rows of up to 256 sites are staged by tensor-map boxes of
+// runs of three rows (or one box of all 48 when the runs are dense), each
+// run at a 128-byte aligned place in shared memory (run_stride); longer rows
+// by one bulk copy per storage slot.  Warp 0, which issues the copies, is always
 // whole (nx / 2 >= 32 threads); the last warp of a block may be partial.
 // flame_step uses the kernel for the row lengths where it is faster
 // (row_kernel_wins).
@@ -475,6 +475,14 @@ constexpr int kHalo = 8;
 // Width of a staged row: the row itself, or a segment with its halos.
 __host__ __device__ constexpr int staged_width(int nx, int H) { return H == 1 ? nx : nx / H + 2 * kHalo; }
 
+// Values between the starts of two runs of three staged rows.  A tensor
+// copy's shared-memory destination must be 128-byte aligned, so for rows
+// staged by boxes the run is padded to a multiple of 64 16-bit values (no
+// padding when nx is a multiple of 64); bulk-copied rows are dense.
+__host__ __device__ constexpr int run_stride(int nx, int H) {
+  return H == 1 && nx <= kBoxMaxX ? (3 * nx + 63) / 64 * 64 : 3 * staged_width(nx, H);
+}
+
 // The site pair (2t, 2t + 1) of a staged tile: ld(s, d) reads staged
 // storage slot s at the pair moved by d sites (d = -c_x reads velocity c on
 // an odd step; d = 0 on even steps), st(s, d, v) writes it there.  NX > 0
@@ -484,8 +492,9 @@ __host__ __device__ constexpr int staged_width(int nx, int H) { return H == 1 ? 
 template <class T, bool ODD, int NX, int H = 1>
 struct PairAccess {
   const T* R;
-  int nx, x0, x1, xm0, xp1;  // nx: the staged row width
-  __device__ __forceinline__ PairAccess(const T* rows, int n) : R(rows), nx(staged_width(NX ? NX : n, H)) {
+  int nx, rs, x0, x1, xm0, xp1;  // nx: the staged row width; rs: the run stride
+  __device__ __forceinline__ PairAccess(const T* rows, int n)
+      : R(rows), nx(staged_width(NX ? NX : n, H)), rs(run_stride(NX ? NX : n, H)) {
     if constexpr (H == 1) {
       x0 = 2 * threadIdx.x;
       x1 = x0 + 1;
@@ -499,13 +508,13 @@ struct PairAccess {
     }
   }
   __device__ __forceinline__ f2 ld(int s, int d) const {
-    const T* r = R + s * nx;
+    const T* r = R + (s / 3) * rs + (s % 3) * nx;
     if (!ODD || d == 0) return Codec2<T>::dec(r + x0);
     if (d < 0) return pack(Codec<T>::dec(r[xm0]), Codec<T>::dec(r[x0]));
     return pack(Codec<T>::dec(r[x1]), Codec<T>::dec(r[xp1]));
   }
   __device__ __forceinline__ void st(int s, int d, f2 v) const {
-    T* r = const_cast<T*>(R) + s * nx;
+    T* r = const_cast<T*>(R) + (s / 3) * rs + (s % 3) * nx;
     if (!ODD || d == 0) {
       Codec2<T>::enc(r + x0, v);
     } else if (d < 0) {
@@ -565,7 +574,7 @@ struct PairGlobal {
 template <class T, bool ODD, int H = 1>
 struct RowIO {
   T* state;
-  T* rows;  // [stage][48 storage slots][staged_width(nx, H)]
+  T* rows;  // [stage][16 runs, run_stride(nx, H) apart][3 storage slots][staged_width(nx, H)]
   unsigned long long* bars;
   long long n3;
   int nx, ny, nz, z0;  // tile t is the row (y, z) = (r % ny, r / ny + z0), r = t / H
@@ -573,6 +582,7 @@ struct RowIO {
   int lane;
   bool boxed, stall;
   const RowMaps* maps;
+  int rs;  // run_stride(nx, H)
 
   __device__ __forceinline__ void issue(int tile, int st) const {
     if constexpr (H > 1) {
@@ -581,16 +591,17 @@ struct RowIO {
     }
     const int y = tile % ny, z = tile / ny + z0;
     const unsigned bar = smem_addr(&bars[st]);
-    T* dst = rows + (size_t)st * kPop * nx;
+    T* dst = rows + (size_t)st * kRuns * rs;
     if (lane == 0) mbar_expect_tx(bar, kPop * rowbytes);
     __syncwarp();
     if (stall) return;
     if (boxed) {
-      if (!ODD) {
+      if (!ODD && rs == 3 * nx) {
+        // dense runs: one box of all 48 storage slots
         if (lane == 0) tensor_load(smem_addr(dst), &maps->all, y, z, 0, bar);
       } else if (lane < kRuns) {
-        tensor_load(smem_addr(dst + 3 * lane * nx), &maps->run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz),
-                    3 * lane, bar);
+        const int ys = ODD ? wrap(y + run_dy(lane), ny) : y, zs = ODD ? wrap(z + run_dz(lane), nz) : z;
+        tensor_load(smem_addr(dst + lane * rs), &maps->run, ys, zs, 3 * lane, bar);
       }
     } else {
       for (int s = lane; s < kPop; s += 32) {
@@ -643,13 +654,13 @@ struct RowIO {
   template <int STAGES, bool DEFER>
   __device__ __forceinline__ void store(int tile, int st) const {
     const int y = tile % ny, z = tile / ny + z0;
-    const T* src = rows + (size_t)st * kPop * nx;
+    const T* src = rows + (size_t)st * kRuns * rs;
     if (boxed) {
-      if (!ODD) {
+      if (!ODD && rs == 3 * nx) {
         if (lane == 0) tensor_store(&maps->all, y, z, 0, smem_addr(src));
       } else if (lane < kRuns) {
-        tensor_store(&maps->run, wrap(y + run_dy(lane), ny), wrap(z + run_dz(lane), nz), 3 * lane,
-                     smem_addr(src + 3 * lane * nx));
+        const int ys = ODD ? wrap(y + run_dy(lane), ny) : y, zs = ODD ? wrap(z + run_dz(lane), nz) : z;
+        tensor_store(&maps->run, ys, zs, 3 * lane, smem_addr(src + lane * rs));
       }
     } else {
       for (int s = lane; s < kPop; s += 32) {
@@ -687,8 +698,8 @@ __global__ void __launch_bounds__(row_bound_threads(NX, H), row_bound_blocks(NX,
   extern __shared__ __align__(128) unsigned char smem[];
   const int nx = NX ? NX : g.nx, ny = g.ny, nz = g.nz;
   const unsigned rowbytes = static_cast<unsigned>(nx) * sizeof(T);
-  const unsigned stagebytes = static_cast<unsigned>(kPop * staged_width(nx, H) * sizeof(T));
-  T* rows = reinterpret_cast<T*>(smem);  // [stage][48 storage slots][staged_width(nx, H)]
+  const unsigned stagebytes = static_cast<unsigned>(kRuns * run_stride(nx, H) * sizeof(T));
+  T* rows = reinterpret_cast<T*>(smem);  // [stage][16 runs][3 storage slots][staged_width(nx, H)]
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kRowStages * stagebytes);
   const int ntiles = ny * g.nzi * H;  // rows (or row segments) of the updated planes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -701,7 +712,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX, H), row_bound_blocks(NX,
   __syncthreads();
 
   const RowIO<T, ODD, H> io{state, rows, bars, g.n3, nx, ny, nz, g.z0, rowbytes, lane, boxed && H == 1,
-                           wt.stall != 0, &maps};
+                           wt.stall != 0, &maps, run_stride(nx, H)};
 
   const int first = blockIdx.x, stride = gridDim.x;
   // Tiles staged before the loop: both stages with two; with three, two of
@@ -841,7 +852,7 @@ __global__ void __launch_bounds__(row_bound_threads(NX, H), row_bound_blocks(NX,
 }
 
 size_t row_smem_bytes(int nx, size_t elem, int stages, int H = 1) {
-  return stages * (kPop * (size_t)staged_width(nx, H) * elem + sizeof(unsigned long long));
+  return stages * (kRuns * (size_t)run_stride(nx, H) * elem + sizeof(unsigned long long));
 }
 
 // Stages per row length, from timings at 128^3, 256^3 and 512^3 (FP16).
@@ -913,7 +924,7 @@ cudaError_t row_launch(const RowCall& c) {
 template <class T, bool ODD, int VAR>
 cudaError_t row_nx(const RowCall& c) {
   // the alignment the staging copies need (see the requirements above)
-  if (c.g.nx <= kBoxMaxX ? c.g.nx % 64 != 0 : c.g.nx % 8 != 0) return cudaErrorInvalidValue;
+  if (c.g.nx % 8 != 0) return cudaErrorInvalidValue;
   if (c.segments == 2) {
     if (c.g.nx <= kBoxMaxX || c.g.nx % 16 != 0) return cudaErrorInvalidValue;
     return c.g.nx == 512 ? row_launch<T, ODD, 512, 2, VAR, 2>(c) : row_launch<T, ODD, 0, 2, VAR, 2>(c);

@@ -26,14 +26,14 @@ def test_reference_arm_prints_the_contract_line():
 
 def test_bench_names_the_kernel_flame_step_uses():
     """bench.py's kernel_name mirrors the library's dispatch: the row kernel
-    for 16-bit storage at nx a multiple of 64 up to 256 and of 8 from 264 to
-    1024 (the alignment its staging copies need), on half rows from 513 to
-    640 sites where nx is a multiple of 16, the one-site kernel between them
-    and otherwise, for FP32 and when forced."""
+    for 16-bit storage at nx a multiple of 8 (whole 16-byte rows) from 96 to
+    1024 and at 64, on half rows from 513 to 640 sites where nx is a
+    multiple of 16, the one-site kernel between them and otherwise, for FP32
+    and when forced."""
     sys.path.insert(0, ROOT)
     import bench
     for n in range(8, 1100, 8):
-        stageable = 64 <= n <= 1024 and (n % 64 == 0 if n <= 256 else True)
+        stageable = (96 <= n <= 1024 or n == 64) and n % 8 == 0
         half = 512 < n <= 640 and n % 16 == 0
         row = stageable and (half or not 512 < n <= 640)
         for st in ("fp16", "bf16"):

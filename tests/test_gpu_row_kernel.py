@@ -2,8 +2,9 @@
 two sites per thread in packed FP32 pairs) against the FP64 oracle and
 against the one-site kernel, for the paper's scheme and its variants (BGK
 fluid, electron MHD, finite-difference current).  Row lengths 64, 128, 256
-and 512 take the compile-time row length instantiations, 192, 328, 960, 1000
-and 1024 the general one (328 and 1000: blocks whose last warp is partial)."""
+and 512 take the compile-time row length instantiations, 72, 192, 200, 328,
+960, 1000 and 1024 the general one (72, 328 and 1000: blocks whose last warp
+is partial; 72 and 200: runs of staged rows padded to 128 bytes)."""
 import numpy as np
 import pytest
 
@@ -38,7 +39,7 @@ def _thin(shape):
 # single-plane lattices, where a row's periodic y / z neighbours are the row
 # itself
 SHAPES = [(6, 5, 64), (4, 3, 128), (3, 4, 192), (2, 3, 512), (1, 1, 64), (1, 2, 256), (2, 1, 960), (1, 2, 1024),
-          (1, 2, 328), (2, 1, 1000)]
+          (1, 2, 328), (2, 1, 1000), (3, 2, 72), (2, 3, 200)]
 B0 = np.array([0.0, 0.02, 0.05])
 
 
@@ -66,15 +67,15 @@ def test_row_kernel_vs_oracle(shape, storage):
     density), per population group (fluid, magnetic) and for the worst single
     population slot, at the TOL bounds above."""
     u, B = _fields(shape, 41)
-    fg, mg, fo, mo = run_both(shape, 0.52, 0.55, 1.5, u, B, 21, storage=storage, literal=False, Bref=tuple(B0))
+    fg, mg, fo, mo = run_both(shape, 0.52, 0.55, 1.5, u, B, 21, storage=storage, literal=False, Bref=tuple(B0),
+                              kernel="row")
     _check_vs_oracle(shape, fg, mg, fo, mo, TOL[storage])
 
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("storage,ulps,steps", [("fp16", 2.0 ** -11, 51), ("bf16", 2.0 ** -8, 101)])
 def test_row_kernel_agrees_with_site_kernel(shape, storage, ulps, steps):
-    """Same fields, 51 (FP16) or 101 (BF16) steps, kernel "auto" (row kernel)
-    vs "site": both compute the collision in FP32 in a different order, so
+    """Same fields, 51 (FP16) or 101 (BF16) steps, kernel "row" vs "site": both compute the collision in FP32 in a different order, so
     the stored deviations differ by a few units of the storage's last place --
     and do differ somewhere, which shows that the row kernel ran (BF16's
     8-bit significand absorbs most ordering differences: on the single-row
@@ -85,7 +86,7 @@ def test_row_kernel_agrees_with_site_kernel(shape, storage, ulps, steps):
     nz, ny, nx = shape
     u, B = _fields(shape, 43)
     pops = []
-    for kernel in ("auto", "site"):
+    for kernel in ("row", "site"):
         sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), kernel=kernel)
         sim.init(None, u, B)
         sim.step(steps)
@@ -122,7 +123,8 @@ def test_row_kernel_graph_replay_is_bit_identical():
 # collision), 256 (three stages, in-place TMA stores), 512 and 960 (two
 # stages, direct stores; compile-time and general row length)
 @pytest.mark.parametrize("shape,storage", [((4, 3, 64), "fp16"), ((2, 3, 256), "bf16"), ((2, 3, 512), "fp16"),
-                                           ((2, 1, 960), "bf16"), ((1, 2, 328), "fp16")])
+                                           ((2, 1, 960), "bf16"), ((1, 2, 328), "fp16"), ((2, 2, 72), "bf16"),
+                                           ((2, 2, 200), "fp16")])
 def test_wait_limit_on_every_pipeline(shape, storage, variant="flame"):
     """A stalled step (barriers armed, copies never issued, 256 polls) on
     each pipeline of the row kernel reports FLAME_ERR_TIMEOUT, leaves the
@@ -132,8 +134,8 @@ def test_wait_limit_on_every_pipeline(shape, storage, variant="flame"):
     from paper_2212_11024_gb300.flame import FLAME_ERR_TIMEOUT
     nz, ny, nx = shape
     u, B = _fields(shape, 49)
-    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), variant=variant)
-    ref = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), variant=variant)
+    sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), variant=variant, kernel="row")
+    ref = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), variant=variant, kernel="row")
     for s in (sim, ref):
         s.init(None, u, B)
         s.step(2)
@@ -205,7 +207,7 @@ def test_row_kernel_wait_limit_reports_timeout():
 
 # the variants on compile-time (64, 256) and general (192, 960: bulk row
 # copies) row lengths, including a single-row lattice
-VARIANT_SHAPES = [(6, 5, 64), (3, 4, 192), (2, 3, 256), (2, 1, 960), (1, 1, 64), (2, 1, 456)]
+VARIANT_SHAPES = [(6, 5, 64), (3, 4, 192), (2, 3, 256), (2, 1, 960), (1, 1, 64), (2, 1, 456), (2, 2, 136)]
 
 
 def _variant_run(shape, storage, kernel, variant, steps, seed):
@@ -230,7 +232,7 @@ def test_row_kernel_variants_vs_oracle(shape, variant, storage):
     the oracle's variant, field by field, per population group and slot, at
     the TOL_VARIANT bounds above."""
     nz, ny, nx = shape
-    u, B, fg, mg = _variant_run(shape, storage, "auto", variant, 21, 51)
+    u, B, fg, mg = _variant_run(shape, storage, "row", variant, 21, 51)
     p = O.Params(nx, ny, nz, 0.52, 0.55, 1.5)
     fo = O.init(p, None, u, B)
     O.step_variant(p, fo, 21, variant, literal=False)
@@ -244,7 +246,7 @@ def test_row_kernel_variants_agree_with_site_kernel(shape, variant):
     """FP16, 51 steps of each variant, row kernel vs one-site kernel: at most
     12 half-precision units of the last place apart (4.2 measured on GB300),
     and apart somewhere (the row kernel ran)."""
-    pops = [_variant_run(shape, "fp16", kernel, variant, 51, 53)[2] for kernel in ("auto", "site")]
+    pops = [_variant_run(shape, "fp16", kernel, variant, 51, 53)[2] for kernel in ("row", "site")]
     a, b = pops
     dev = np.abs(b - np.median(b, axis=(1, 2, 3), keepdims=True)).max()
     d = np.abs(a - b)
