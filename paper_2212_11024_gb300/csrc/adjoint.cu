@@ -33,7 +33,8 @@
 namespace flame {
 namespace {
 
-// 64-thread blocks, ten per SM (96 registers, no spills).  The lambda gather
+// 96 registers without spills: 64-thread blocks, ten per SM, for FP32
+// storage; 128-thread blocks, five per SM, for 16-bit storage.  The lambda gather
 // goes into shared memory by asynchronous copies (cp.async) that are in
 // flight during the forward recompute, and lambda is read from there where
 // it is used rather than held in registers; for 16-bit storage the state
@@ -51,11 +52,15 @@ namespace {
 // per-storage load order and 64 x 10, 10.51 / 11.16 with read-only state
 // loads and 256-byte L2 prefetch hints on them and on the lambda copies
 // (10.46 / 11.06 for the state loads alone; f32x2 pairs inside the 1-D
-// passes: 10.35 / 11.04, not kept).  (Per-warp sums in FP32 gained 0.7 %
+// passes: 10.35 / 11.04, not kept); with the hints, 128 x 5 10.52 / 11.31
+// against 64 x 10 10.57 / 11.23, hence the block per storage (128-byte
+// state prefetch: 10.51 / 11.18).  (Per-warp sums in FP32 gained 0.7 %
 // but, where the sites' terms cancel -- a random lambda: sum |a| / |sum a|
 // ~ 5000 -- they added ~5x the rounding of the per-site arithmetic to d_i.)
-constexpr int kAdjThreads = 64;
-constexpr int kAdjMinBlocks = 10;
+template <class T>
+constexpr int kAdjThreads = sizeof(T) == 2 ? 128 : 64;
+template <class T>
+constexpr int kAdjMinBlocks = sizeof(T) == 2 ? 5 : 10;
 
 // 1-D functions of the undivided equilibrium and inverse-moment maps, and
 // their derivatives in u, at velocity component c (index p = c + 1).
@@ -183,14 +188,14 @@ struct LamSlots {
 };
 
 template <class T, bool ODD>
-__global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
+__global__ void __launch_bounds__(kAdjThreads<T>, kAdjMinBlocks<T>)
     adjoint_step_kernel(Slots<T> P, Grid g, StepConsts k, const __grid_constant__ LamSlots L,
                         double* __restrict__ partials) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z + g.z0;
   const bool live = x < g.nx && y < g.ny;
-  __shared__ float lsm[kPop][kAdjThreads];
+  __shared__ float lsm[kPop][kAdjThreads<T>];
   double abar_site = 0.0;
   if (live) {
     const int site = (z * g.ny + y) * g.nx + x;
@@ -721,8 +726,9 @@ inline void sum_partials(double* partials, long long n, double* out, cudaStream_
 
 template <class T>
 cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, const float* lin, float* lout,
-                      double* partials, long long nblk, double* ddi, cudaStream_t s) {
-  const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
+                      double* partials, double* ddi, cudaStream_t s) {
+  const dim3 b = site_block(g, kAdjThreads<T>), gr = site_grid(g, b);
+  const long long nblk = (long long)gr.x * gr.y * gr.z;
   const Slots<T> P = make_slots<T>(pop, g);
   LamSlots L;
   for (int q = 0; q < kPop; ++q) {
@@ -740,20 +746,25 @@ cudaError_t adjoint_t(int odd, const void* pop, Grid g, const StepConsts& k, con
 }  // namespace
 
 long long adjoint_partials_needed(Grid g) {
-  const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
+  // per warp of the step kernel (either block shape), per block of the
+  // initialisation adjoint
+  long long need = 0;
+  for (int threads : {kAdjThreads<float>, kAdjThreads<__half>}) {
+    const dim3 b = site_block(g, threads), gr = site_grid(g, b);
+    const long long a = (long long)gr.x * gr.y * gr.z * ((b.x * b.y) >> 5);
+    if (a > need) need = a;
+  }
   const dim3 bi = site_block(g, 128), gi = site_grid(g, bi);
-  const long long a = (long long)gr.x * gr.y * gr.z * ((b.x * b.y) >> 5), c = (long long)gi.x * gi.y * gi.z;
-  return (a > c ? a : c) + kSumBlocks;
+  const long long c = (long long)gi.x * gi.y * gi.z;
+  return (need > c ? need : c) + kSumBlocks;
 }
 
 cudaError_t launch_step_adjoint(int storage, int odd, const void* pop, Grid g, const StepConsts& k, const float* lin,
                                 float* lout, double* partials, double* ddi, cudaStream_t s) {
-  const dim3 b = site_block(g, kAdjThreads), gr = site_grid(g, b);
-  const long long nblk = (long long)gr.x * gr.y * gr.z;
   switch (storage) {
-    case 1: return adjoint_t<float>(odd, pop, g, k, lin, lout, partials, nblk, ddi, s);
-    case 2: return adjoint_t<__half>(odd, pop, g, k, lin, lout, partials, nblk, ddi, s);
-    case 3: return adjoint_t<__nv_bfloat16>(odd, pop, g, k, lin, lout, partials, nblk, ddi, s);
+    case 1: return adjoint_t<float>(odd, pop, g, k, lin, lout, partials, ddi, s);
+    case 2: return adjoint_t<__half>(odd, pop, g, k, lin, lout, partials, ddi, s);
+    case 3: return adjoint_t<__nv_bfloat16>(odd, pop, g, k, lin, lout, partials, ddi, s);
   }
   return cudaErrorInvalidValue;
 }
