@@ -247,6 +247,55 @@ def test_full_size_sampled_sites_256():
     sim.close()
 
 
+def test_full_size_sampled_sites_512():
+    """512^3 FP16 (the lattice of the d_i sweep; rows of 512 sites take the
+    row kernel's direct stores, slot planes of 134 M sites, a state of more
+    than 2^32 values): Orszag-Tang fields (Sec. 4.4) scaled to the sweep's
+    velocities, d_i = 25.6, tau = 0.51; one even and one odd step, each
+    checked at 16 sampled sites against the oracle's literal collision of the
+    GPU's own pre-step populations, streamed (the sites include the lattice's
+    last plane, row and column, where the periodic wrap and the largest
+    offsets meet)."""
+    from paper_2212_11024_gb300 import Flame
+    import torch
+    N = 512
+    # the Orszag-Tang fields of inputs.orszag_tang (u0 = 1, b0 = 0.8, scale
+    # 0.02), built on the device in FP32 (12.9 GB of FP64 fields on the host
+    # would be needless)
+    q = torch.arange(N, device="cuda", dtype=torch.float32) * (2 * np.pi / N)
+    X, Y, Z = q.view(1, 1, N), q.view(1, N, 1), q.view(N, 1, 1)
+    full = (N, N, N)
+    u = torch.stack([(-2 * torch.sin(Y)).expand(full), (2 * torch.sin(X)).expand(full),
+                     torch.zeros(full, device="cuda")]) * 0.02
+    B = torch.stack([(-2 * torch.sin(2 * Y) + torch.sin(Z)).expand(full), (2 * torch.sin(X) + torch.sin(Z)).expand(full),
+                     (torch.sin(X) + torch.sin(Y)).expand(full)]) * (0.8 * 0.02)
+    sim = Flame(N, N, N, 0.51, 0.51, 25.6, storage="fp16")
+    sim.init(None, u, B)
+    del u, B
+    rng = np.random.default_rng(1)
+    C, _, XI, _ = O.lattice()
+    vel = np.concatenate([C, XI, XI, XI])
+    rest = rest_populations((1, 1, 1))[:, 0, 0, 0]
+    sites = [(N - 1, N - 1, N - 1), (N - 1, 0, N - 1), (0, N - 1, 0)] + [tuple(rng.integers(0, N, 3)) for _ in range(13)]
+    for parity in (0, 1):
+        assert sim.info()["parity"] == parity
+        f0 = sim.populations()
+        sim.step(1)
+        f1 = sim.populations()
+        worst = 0.0
+        for z, y, x in sites:
+            pre = f0[:, z, y, x].cpu().numpy()
+            post, _ = O.site_collide(pre, 0.51, 0.51, 25.6, literal=True)
+            idx = [((z + c[2]) % N, (y + c[1]) % N, (x + c[0]) % N) for c in vel]
+            got = np.array([float(f1[q, i[0], i[1], i[2]]) for q, i in enumerate(idx)])
+            worst = max(worst, np.abs(got - post).max() / np.abs(post - rest).max())
+        assert worst < 2e-3, (parity, worst)
+        del f0, f1
+        torch.cuda.empty_cache()
+    assert sim.sync() is None
+    sim.close()
+
+
 def test_probe_and_graph_stepping():
     """flame_probe returns the moments of the listed sites (invalid index ->
     NaN); graph_steps replays give bit-identical states to single launches
