@@ -96,6 +96,50 @@ def test_step_adjoint_matches_autograd(storage, nsteps, shape):
     assert abs(float(ddi[0]) - ref_d) < tol
 
 
+@pytest.mark.parametrize("storage,nsteps", [("fp16", 3), ("fp32", 4)])
+def test_step_adjoint_full_size_sampled_sites(storage, nsteps):
+    """256^3 (the adjoint's benchmark lattice, d_i = 12.8, tau = 0.51), both
+    AA parities: lambda_t at 16 sampled sites (including the lattice's last
+    plane, row and column) against autograd of the torch restatement's
+    collision of that site alone, with lambda_{t+1} gathered from x + c_q.
+    lambda_t at a site depends only on its own state and on that gather, so
+    the full-size launch is checked site by site."""
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    from paper_2212_11024_gb300.flame import library
+    N = 256
+    u, B = turbulence((N, N, N), 3, 0.05, shells=(1, 4))
+    sim = Flame(N, N, N, 0.51, 0.51, 0.05 * N, storage=storage)
+    sim.init(None, u, B)
+    del u, B
+    sim.step(nsteps)
+    blob, _, par = sim.get_state()
+    pop = sim.populations()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(nsteps)
+    lin = torch.randn((48, N ** 3), dtype=torch.float32, device="cuda", generator=gen)
+    lout = torch.empty_like(lin)
+    ddi = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = library().flame_step_adjoint(sim._ctx, ctypes.c_void_p(blob.data_ptr()), par, ctypes.c_void_p(lin.data_ptr()),
+                                      ctypes.c_void_p(lout.data_ptr()), ctypes.c_void_p(ddi.data_ptr()))
+    assert rc == 0
+    torch.cuda.synchronize()
+    vel = R._velocities().numpy()
+    rng = np.random.default_rng(nsteps)
+    sites = [(N - 1, N - 1, N - 1), (0, N - 1, 0), (N - 1, 0, N - 1)] + [tuple(rng.integers(0, N, 3)) for _ in range(13)]
+    worst = 0.0
+    for z, y, x in sites:
+        pre = torch.tensor(pop[:, z, y, x].cpu().numpy()[None, :], requires_grad=True)
+        gathered = [float(lin[q, (((z + c[2]) % N) * N + (y + c[1]) % N) * N + (x + c[0]) % N]) for q, c in enumerate(vel)]
+        post = R.site_collide(pre, 0.51, 0.51, torch.tensor(0.05 * N, dtype=torch.float64))
+        (g,) = torch.autograd.grad((post[0] * torch.tensor(gathered, dtype=torch.float64)).sum(), [pre])
+        ref = g[0].numpy()
+        got = lout[:, (z * N + y) * N + x].double().cpu().numpy()
+        worst = max(worst, float(np.abs(got - ref).max() / np.abs(ref).max()))
+    sim.close()
+    assert worst < 1e-5, worst
+
+
 def test_init_adjoint_matches_autograd():
     from paper_2212_11024_gb300 import Flame
     from paper_2212_11024_gb300.flame import library
