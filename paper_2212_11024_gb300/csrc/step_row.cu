@@ -50,7 +50,7 @@ cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 // many segments per tile.  Timed with FP16 storage on ~4M-site lattices
 // (nx x m x m, GLUPS; whole rows / half rows / one-site): 72 18.6 / - /
 // 18.9, 96 24.5 / - / 23.5, 120 28.2 / - / 23.2, 136 21.3 / - / 20.5, 160
-// 25.2 / - / 22.6, 200 23.9 / - / 21.9, 224 26.4 / - / 23.3, 248 28.8 / - /
+// 25.2 / - / 22.6, 200 26.5 / - / 21.9, 224 28.8 / - / 23.3, 248 28.8 / - /
 // 23.6, 256 31.9 / - / 24.2, 264 24.5 / - / 18.9, 320 29.2 / 20.6 / 21.2, 328 24.3 / - / 20.7,
 // 384 26.6 / 22.0 / 22.5, 400 26.7 / 21.8 / 22.0, 448 27.6 / 21.9 / 22.8,
 // 456 26.7 / - / 23.0, 504 28.5 / - / 24.1, 512 30.7 / 27.5 / 24.4, 520

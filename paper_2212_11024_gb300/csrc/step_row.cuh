@@ -861,9 +861,11 @@ size_t row_smem_bytes(int nx, size_t elem, int stages, int H = 1) {
 // 256-site rows (32.9 GLUPS against 32.15 for three stages of three
 // blocks, where the store of a tile drains while the next one computes),
 // and one block instead of two at 512-site rows with three (17.5 against
-// 30.1).  The general instantiation keeps three stages between 129 and 255
-// sites (192: the refill inside the collision was not timed there).
-constexpr int row_stages(int nx) { return nx > 128 && nx < 256 ? 3 : 2; }
+// 30.1).  The general instantiation: three stages with TMA stores from 129
+// to 199 sites, two with direct stores from 200 (~4M-site lattices, GLUPS
+// three / two stages: 136 21.2 / 20.7, 160 25.2 / 24.2, 200 23.9 / 26.5,
+// 224 26.5 / 28.8, 248 28.8 / 28.6; 192: 29.4 with three).
+constexpr int row_stages(int nx) { return nx > 128 && nx < 200 ? 3 : 2; }
 
 // Launch configuration of one instantiation, cached per device (the
 // shared-memory opt-in and the resident blocks per SM depend on the device
