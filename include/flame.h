@@ -102,17 +102,17 @@ typedef struct {
                          captures the graph that starts at parity 0                      */
     int variant;      /* flame_variant (FLAME_SCHEME = 0 by default); the adjoint
                          entry points support FLAME_SCHEME only                          */
-    int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant), a 16-byte
-                         aligned state and nx a multiple of 8 from 96 to 1024, or 64,
-                         use the row kernel (x rows staged in shared memory,
-                         two sites per thread in packed FP32 pairs; half a row per tile
-                         from 513 to 640 sites where nx is a multiple of 16, a whole row
-                         below 513 and above 640: the faster tilings as timed), everything
-                         else -- and 513..640 with nx not a multiple of 16 -- the one-site
-                         kernel; 1: always the one-site kernel; 2: the
-                         row kernel with a whole row per block tile, 3: with half a row
-                         per tile (rows of more than 256 sites, nx a multiple of 16),
-                         where the row kernel applies, else the one-site kernel.  All compute the same step in FP32; results
+    int kernel;       /* 0: automatic -- FP16/BF16 storage (any variant) with nx even
+                         uses the row kernel (two sites per thread in packed FP32
+                         pairs), in the tiling timed fastest for the row length: x rows
+                         staged in shared memory by TMA, a whole row per block tile
+                         (most lengths that are multiples of 8 from 64 to 1024) or half a
+                         row (608, 624, 640), or unstaged pairs loaded and stored
+                         straight from HBM (every other even length); odd nx and FP32
+                         storage use the one-site kernel; 1: always the one-site kernel;
+                         2: staged whole rows (nx a multiple of 8 in 64..1024), 3: staged
+                         half rows (nx > 256 a multiple of 16), 4: unstaged pairs (nx
+                         even), where they apply, else the one-site kernel.  All compute the same step in FP32; results
                          agree to FP32 rounding before encoding (the row kernel's tilings
                          agree bit for bit). */
     int halo_z;       /* 0: a periodic nx x ny x nz lattice.  1: one z-slab of a larger

@@ -81,7 +81,7 @@ flame_status check_params(const flame_params* p) {
   if (p->check_every < 0) return FLAME_ERR_PARAM;
   if (p->graph_steps < 0 || (p->graph_steps & 1)) return FLAME_ERR_PARAM;
   if (p->variant < FLAME_SCHEME || p->variant > FLAME_FD_CURRENT) return FLAME_ERR_PARAM;
-  if (p->kernel < 0 || p->kernel > 3) return FLAME_ERR_PARAM;
+  if (p->kernel < 0 || p->kernel > 4) return FLAME_ERR_PARAM;
   return FLAME_OK;
 }
 
@@ -749,7 +749,7 @@ flame_status flame_debug_stall_next_step(flame_ctx* c, unsigned tries) {
   flame_status st = usable(c);
   if (st != FLAME_OK) return st;
   if (!c->initialized) return FLAME_ERR_STATE;
-  if (tries == 0 || !flame::step_row_supported(c->g, c->p.storage, c->p.variant, c->state, c->p.kernel))
+  if (tries == 0 || !flame::step_row_staged(c->g, c->p.storage, c->p.variant, c->state, c->p.kernel))
     return FLAME_ERR_PARAM;
   c->stall_tries = tries;
   return FLAME_OK;

@@ -38,20 +38,26 @@ constexpr int kVarFdCurrent = 3;  // J from the central-difference curl of B
 // pre-collision B - B_ref, [3][N3] values of the storage's element type,
 // required by kVarFdCurrent only.
 // kernel (flame_params.kernel): 0 the row kernel where step_row_supported
-// (whole rows or half rows as row_auto_segments chooses), else the one-site
-// kernel; 1 always the one-site kernel; 2 the row kernel on whole rows and
-// 3 on half rows, where they apply (else the one-site kernel).
+// (whole rows, half rows or the unstaged pair kernel as row_segments
+// chooses), else the one-site kernel; 1 always the one-site kernel; 2 the
+// row kernel on whole rows, 3 on half rows and 4 the pair kernel, where they
+// apply (else the one-site kernel).
 cudaError_t launch_step(int storage, int odd, void* pop, Grid g, const StepConsts& k, unsigned* flag,
                         cudaStream_t s, int variant = kVarFlame, void* Bfd = nullptr, int kernel = 0);
 
-// The step for 16-bit storage as a persistent kernel over x rows staged in
-// shared memory (step_row.cuh), two sites per thread in packed FP32 pairs:
-// every variant, 64 <= nx <= 1024 with nx a multiple of 8 (automatic choice:
-// where the row kernel is the faster one), a 16-byte aligned state; half
-// rows for nx > 256 a multiple of 16 only.  flag bit 1: a
+// The step for 16-bit storage, two sites per thread in packed FP32 pairs
+// (step_row.cuh): as a persistent kernel over x rows staged in shared memory
+// (64 <= nx <= 1024 with nx a multiple of 8, a 16-byte aligned state; half
+// rows for nx > 256 a multiple of 16 only), or unstaged (the pair kernel,
+// any even nx); every variant.  Automatic choice: the faster of these by row
+// length, for every even nx.  flag bit 1: a
 // non-finite moment; bit 2: a staged copy did not complete within the wait
 // limit.
 bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel = 0);
+// The segments per tile launch_step_row uses (0: the pair kernel, no staging).
+int row_segments(int nx, int kernel);
+// step_row_supported with staged rows (the kernels whose copies have waits).
+bool step_row_staged(Grid g, int storage, int variant, const void* pop, int kernel = 0);
 // Settles the launch configuration of the kernel launch_step would use
 // (no launch); needed once before stream capture.
 cudaError_t prepare_step(int storage, const void* pop, Grid g, int variant, int kernel);

@@ -46,55 +46,64 @@ cudaError_t row_maps(const void* pop, const Grid& g, RowMaps* out) {
 
 cudaError_t step_row_flame(const RowCall& c) { return row_call<kVarFlame>(c); }
 
-// Row lengths where the row kernel beats the one-site kernel, and with how
-// many segments per tile.  Timed with FP16 storage on ~4M-site lattices
-// (nx x m x m, GLUPS; whole rows / half rows / one-site): 72 18.6 / - /
-// 18.9, 96 24.5 / - / 23.5, 120 28.2 / - / 23.2, 136 21.3 / - / 20.5, 160
-// 25.2 / - / 22.6, 200 26.5 / - / 21.9, 224 28.8 / - / 23.3, 248 28.8 / - /
-// 23.6, 256 31.9 / - / 24.2, 264 24.5 / - / 18.9, 320 29.2 / 20.6 / 21.2, 328 24.3 / - / 20.7,
-// 384 26.6 / 22.0 / 22.5, 400 26.7 / 21.8 / 22.0, 448 27.6 / 21.9 / 22.8,
-// 456 26.7 / - / 23.0, 504 28.5 / - / 24.1, 512 30.7 / 27.5 / 24.4, 520
-// 19.6 / - / 20.7, 528 20.1 / 22.5 / 20.9, 544 20.8 / 23.2 / 21.3, 552 20.8
-// / - / 21.3, 560 21.3 / 24.0 / 21.5, 568 21.3 / - / 21.7, 576 21.9 / 24.4
-// / 21.9, 640 24.2 / 26.7 / 23.0, 704 25.0 / 20.9 / 23.2, 744 26.6 / - /
-// 23.9, 768 27.8 / 24.6 / 24.3, 832 24.6 / 22.2 / 22.2, 896 26.3 / 23.7 /
-// 22.9, 960 27.9 / 23.7 / 23.3, 1000 28.1 / - / 22.7, 1024 29.3 / 26.5 /
-// 23.1 (384, 448 and 704-960 before the direct stores addressed their rows
-// from slot bases, which gained 5-8 % at 320-1024; 64-192 as in earlier
-// timings: 28.0 / 24.1, 31.8 / 24.2, 29.4 / 23.5 whole rows against
-// one-site).  Whole rows win from 96 sites (and at 64) up to 512 and above
-// 640; below 96 a block of under 48 threads carries a tile's copies for too
-// few sites and the one-site kernel is as fast.  Between 512 and 640, a
-// whole row's block of 260-320 threads (128 registers each) fits once per
-// SM; there half rows per tile (three blocks per SM) are the faster tiling
-// where a half row is a whole number of 16-byte units (nx a multiple of
-// 16), and the one-site kernel where it is not.  Elsewhere half rows lose:
-// twice the copies per site (96 per tile on odd steps, the halo across a
-// row's end by a copy of its own) for the same warps per SM.
-bool row_kernel_wins(int nx) {
-  return !((nx > 512 && nx <= 640 && nx % 16 != 0) || (nx < 96 && nx % 64 != 0));
+// The automatic choice among the row kernel's tilings, from a sweep of
+// every multiple of 8 from 64 to 1024 with FP16 storage on ~4M-site
+// lattices (nx x m x m, graph replay, GLUPS).  The unstaged pair kernel runs
+// at 24.6-25.4 at every length; the staged kernel's whole rows run at 28-32
+// where a row's block fits several times per SM and its stages are dense
+// (64 28.1, 128 31.8, 192 29.3, 256 31.9, 320 30.0, 384 29.0, 448 30.3, 512
+// 30.7, 768 28.5, 1024 31.5), and lose to the pair kernel where a block is
+// under 48 threads (72-96: 18.6-24.5), where three stages of padded rows
+// fit few blocks (136-152: 21.2-24.1), where a block of 260-320 threads
+// fits once per SM (520-648: 20.0-24.9, half rows 22.5-26.7, ahead of the
+// pair kernel from 608 where a half row is whole 16-byte units) and at
+// 776-792 (24.4-25.0).  Ties (within 0.3) keep whole rows.  Odd row lengths
+// take the one-site kernel.
+int row_auto_segments(int nx) {
+  if (nx % 8 != 0 || nx < 64 || nx > 1024) return 0;
+  if ((nx > 64 && nx < 104) || (nx > 128 && nx < 160) || (nx >= 776 && nx <= 792)) return 0;
+  if (nx > 512 && nx <= 648) return nx >= 608 && nx % 16 == 0 ? 2 : 0;
+  return 1;
 }
-
-// Segments per tile of the automatic choice (kernel = 0).
-int row_auto_segments(int nx) { return nx > 512 && nx <= 640 ? 2 : 1; }
 
 // Row lengths the row kernel stages: whole 16-byte units per row (up to 256
 // sites by tensor-map boxes of runs placed at 128-byte aligned offsets,
 // longer rows by bulk copies).
 static bool row_length_ok(int nx) { return nx % 8 == 0; }
 
-bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel) {
-  if (kernel == 1) return false;
-  const bool base = variant >= kVarFlame && variant <= kVarFdCurrent && (storage == 2 || storage == 3) &&
-                    g.nx >= 64 && g.nx <= 2 * kRowMaxThreads && row_length_ok(g.nx) &&
-                    (reinterpret_cast<uintptr_t>(pop) & 15u) == 0;
-  if (!base) return false;
-  if (kernel == 3) return g.nx > kBoxMaxX && g.nx % 16 == 0;  // half rows: whole 16-byte units per half
-  if (kernel == 2) return true;
-  return row_kernel_wins(g.nx);
+// The pair kernel: 16-bit storage, any even row length, a 4-byte aligned
+// state (pairs are 32-bit accesses).
+static bool pair_ok(Grid g, int storage, int variant, const void* pop) {
+  return variant >= kVarFlame && variant <= kVarFdCurrent && (storage == 2 || storage == 3) && g.nx % 2 == 0 &&
+         (reinterpret_cast<uintptr_t>(pop) & 3u) == 0;
 }
 
-int row_segments(int nx, int kernel) { return kernel == 3 ? 2 : kernel == 2 ? 1 : row_auto_segments(nx); }
+// The staged tilings: 64 <= nx <= 1024, nx a multiple of 8, a 16-byte
+// aligned state.
+static bool staged_ok(Grid g, int storage, int variant, const void* pop) {
+  return variant >= kVarFlame && variant <= kVarFdCurrent && (storage == 2 || storage == 3) && g.nx >= 64 &&
+         g.nx <= 2 * kRowMaxThreads && row_length_ok(g.nx) && (reinterpret_cast<uintptr_t>(pop) & 15u) == 0;
+}
+
+bool step_row_supported(Grid g, int storage, int variant, const void* pop, int kernel) {
+  switch (kernel) {
+    case 1: return false;
+    case 2: return staged_ok(g, storage, variant, pop);
+    case 3: return staged_ok(g, storage, variant, pop) && g.nx > kBoxMaxX && g.nx % 16 == 0;
+    case 4: return pair_ok(g, storage, variant, pop);
+  }
+  // automatic: the pair kernel or a staged tiling for every even row length
+  return pair_ok(g, storage, variant, pop) &&
+         (row_auto_segments(g.nx) == 0 || staged_ok(g, storage, variant, pop));
+}
+
+int row_segments(int nx, int kernel) {
+  return kernel == 4 ? 0 : kernel == 3 ? 2 : kernel == 2 ? 1 : row_auto_segments(nx);
+}
+
+bool step_row_staged(Grid g, int storage, int variant, const void* pop, int kernel) {
+  return step_row_supported(g, storage, variant, pop, kernel) && row_segments(g.nx, kernel) != 0;
+}
 
 namespace {
 cudaError_t row_variant(int variant, const RowCall& c) {

@@ -39,8 +39,10 @@
 // run at a 128-byte aligned place in shared memory (run_stride); longer rows
 // by one bulk copy per storage slot.  Warp 0, which issues the copies, is always
 // whole (nx / 2 >= 32 threads); the last warp of a block may be partial.
-// flame_step uses the kernel for the row lengths where it is faster
-// (row_kernel_wins).
+// The same packed collision also runs unstaged (step_pair_kernel: loads and
+// stores straight from HBM, any even row length).  flame_step picks among
+// whole rows, half rows and the pair kernel by row length
+// (row_auto_segments).
 #pragma once
 
 #include <cuda.h>
@@ -72,7 +74,8 @@ struct RowWait {
 // current, else unused; launch false only settles the launch configuration.
 struct RowCall {
   int storage, odd;
-  int segments;  // 1: a tile is a whole row; 2: half a row (rows of more than 256 sites)
+  int segments;  // 1: a tile is a whole row; 2: half a row (rows of more than 256 sites);
+                 // 0: no staging (the pair kernel)
   void* pop;
   Grid g;
   StepConsts k;
@@ -547,6 +550,14 @@ struct PairGlobal {
   const SlotBases<T>* base;
   int off[3][3];
   int dm, dp;
+  __device__ __forceinline__ f2 ld(int s, int d) const {
+    const int r = s / 3;
+    const int dy = ODD ? run_dy(r) : 0, dz = ODD ? run_dz(r) : 0;
+    const T* row = base->p[s] + off[dz + 1][dy + 1];
+    if (!ODD || d == 0) return Codec2<T>::dec(row);
+    if (d < 0) return pack(Codec<T>::dec(row[dm]), Codec<T>::dec(row[0]));
+    return pack(Codec<T>::dec(row[1]), Codec<T>::dec(row[1 + dp]));
+  }
   __device__ __forceinline__ void st(int s, int d, f2 v) const {
     const int r = s / 3;
     const int dy = ODD ? run_dy(r) : 0, dz = ODD ? run_dz(r) : 0;
@@ -851,6 +862,79 @@ __global__ void __launch_bounds__(row_bound_threads(NX, H), row_bound_blocks(NX,
   if (warp == 0) bulk_wait_done();
 }
 
+// The pair kernel: the row kernel's packed collision of the site pair
+// (x0, x0 + 1) with its populations loaded from and stored to HBM directly,
+// no staging -- any even row length.  Under the AA pattern a pair writes
+// exactly the places it read (PairGlobal), and the collision reads all of
+// its inputs before it writes (as in the staged rows, which it updates in
+// place), so pairs need no synchronisation.  One pair per thread.
+constexpr int kPairThreads = 128;
+template <class T, bool ODD, int VAR>
+__global__ void __launch_bounds__(kPairThreads, 4)
+    step_pair_kernel(Grid g, StepConsts k, unsigned* __restrict__ flag, const T* __restrict__ Bfd,
+                     const __grid_constant__ SlotBases<T> bases) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz, pairs = nx / 2;
+  const long long p = (long long)blockIdx.x * kPairThreads + threadIdx.x;
+  if (p >= (long long)pairs * ny * g.nzi) return;
+  const int xp = (int)(p % pairs);
+  const long long rowi = p / pairs;
+  const int y = (int)(rowi % ny), z = (int)(rowi / ny) + g.z0;
+  const int gx0 = 2 * xp, gx1 = gx0 + 1;
+  const int gxm0 = gx0 == 0 ? nx - 1 : gx0 - 1, gxp1 = gx1 == nx - 1 ? 0 : gx1 + 1;
+  PairGlobal<T, ODD> G;
+  G.base = &bases;
+  G.dm = gxm0 - gx0;
+  G.dp = gxp1 - gx1;
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+      G.off[dz][dy] =
+          (ODD || (dz == 1 && dy == 1)) ? (wrap(z + dz - 1, nz) * ny + wrap(y + dy - 1, ny)) * nx + gx0 : 0;
+  auto ldf = [&](int px, int py, int pz) {
+    const int q = px + 3 * py + 9 * pz;
+    return G.ld(ODD ? 26 - q : q, 1 - px);
+  };
+  auto ldg = [&](int c, int i) { return G.ld(kQ + 3 * (ODD ? opp7(i) : i) + c, -mx7(i)); };
+  auto stf = [&](int px, int py, int pz, f2 v) {
+    const int q = px + 3 * py + 9 * pz;
+    G.st(ODD ? q : 26 - q, px - 1, v);
+  };
+  auto stg = [&](int c, int i, f2 v) { G.st(kQ + 3 * (ODD ? i : opp7(i)) + c, mx7(i), v); };
+  auto curl_b = [&](f2 (&J)[3]) {
+    const long long r0 = ((long long)z * ny + y) * nx;
+    const long long ryp = ((long long)z * ny + wrap(y + 1, ny)) * nx;
+    const long long rym = ((long long)z * ny + wrap(y - 1, ny)) * nx;
+    const long long rzp = ((long long)wrap(z + 1, nz) * ny + y) * nx;
+    const long long rzm = ((long long)wrap(z - 1, nz) * ny + y) * nx;
+    const T *Bx = Bfd, *By = Bfd + g.n3, *Bz = Bfd + 2 * g.n3;
+    auto at = [&](const T* b, long long r) { return f2{dec2(b + r + gx0)}; };
+    auto one = [&](const T* b, long long i) { return Codec<T>::dec(b[i]); };
+    const f2 by0 = at(By, r0), bz0 = at(Bz, r0);
+    const f2 dxBy = pack(by0.v.y, one(By, r0 + gxp1)) - pack(one(By, r0 + gxm0), by0.v.x);
+    const f2 dxBz = pack(bz0.v.y, one(Bz, r0 + gxp1)) - pack(one(Bz, r0 + gxm0), bz0.v.x);
+    J[0] = 0.5f * ((at(Bz, ryp) - at(Bz, rym)) - (at(By, rzp) - at(By, rzm)));
+    J[1] = 0.5f * ((at(Bx, rzp) - at(Bx, rzm)) - dxBz);
+    J[2] = 0.5f * (dxBy - (at(Bx, ryp) - at(Bx, rym)));
+  };
+  auto mid = [] {};
+  collide_pair<VAR>(ldf, ldg, stf, stg, curl_b, mid, k, flag);
+}
+
+template <class T, bool ODD, int VAR>
+cudaError_t pair_launch(const RowCall& c) {
+  if (c.g.nx % 2 != 0) return cudaErrorInvalidValue;
+  if (!c.launch) return cudaSuccess;
+  const long long npairs = (long long)(c.g.nx / 2) * c.g.ny * c.g.nzi;
+  const long long blocks = (npairs + kPairThreads - 1) / kPairThreads;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  SlotBases<T> bases;
+  for (int sl = 0; sl < kPop; ++sl) bases.p[sl] = static_cast<T*>(c.pop) + (size_t)sl * (size_t)c.g.n3;
+  step_pair_kernel<T, ODD, VAR><<<(unsigned)blocks, kPairThreads, 0, c.s>>>(c.g, c.k, c.flag,
+                                                                         static_cast<const T*>(c.Bfd), bases);
+  return cudaGetLastError();
+}
+
 size_t row_smem_bytes(int nx, size_t elem, int stages, int H = 1) {
   return stages * (kRuns * (size_t)run_stride(nx, H) * elem + sizeof(unsigned long long));
 }
@@ -925,6 +1009,7 @@ cudaError_t row_launch(const RowCall& c) {
 
 template <class T, bool ODD, int VAR>
 cudaError_t row_nx(const RowCall& c) {
+  if (c.segments == 0) return pair_launch<T, ODD, VAR>(c);
   // the alignment the staging copies need (see the requirements above)
   if (c.g.nx % 8 != 0) return cudaErrorInvalidValue;
   if (c.segments == 2) {

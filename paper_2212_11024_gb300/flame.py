@@ -29,7 +29,7 @@ VARIANT = {"flame": 0, "bgk": 1, "emhd": 2, "fd_current": 3}
 # flame_params.kernel: "auto" uses the row kernel (TMA-staged rows, packed
 # FP32 pairs) where it applies, "site" always the one-site kernel, "row" and
 # "row_half" the row kernel with whole or half rows per tile where it applies.
-KERNEL = {"auto": 0, "site": 1, "row": 2, "row_half": 3}
+KERNEL = {"auto": 0, "site": 1, "row": 2, "row_half": 3, "pair": 4}
 NSCALARS = 14
 SCALAR_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "B_x", "B_y", "B_z", "E_u", "E_B", "H_c", "J2", "u_max",
                 "divB_rms", "nonfinite"]

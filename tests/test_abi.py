@@ -65,7 +65,7 @@ def test_state_bytes_and_param_validation(lib):
            F.make_params(4, 4, 4, 0.6, 0.4, 0.0), F.make_params(4, 4, 4, 0.6, 0.6, -1.0),
            F.make_params(4, 4, 4, 0.6, 0.6, 0.0, storage=7), F.make_params(2048, 1024, 1024, 0.6, 0.6, 0.0),
            F.make_params(4, 4, 4, 0.6, 0.6, float("nan")), F.make_params(4, 4, 4, 0.6, 0.6, 0.0, rho0=0.0),
-           F.make_params(4, 4, 4, 0.6, 0.6, 0.0, kernel=4)]
+           F.make_params(4, 4, 4, 0.6, 0.6, 0.0, kernel=5)]
     b = F.make_params(4, 4, 4, 0.6, 0.6, 0.0)
     b.halo_z = 2
     bad.append(b)

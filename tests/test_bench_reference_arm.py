@@ -25,19 +25,21 @@ def test_reference_arm_prints_the_contract_line():
 
 
 def test_bench_names_the_kernel_flame_step_uses():
-    """bench.py's kernel_name mirrors the library's dispatch: the row kernel
-    for 16-bit storage at nx a multiple of 8 (whole 16-byte rows) from 96 to
-    1024 and at 64, on half rows from 513 to 640 sites where nx is a
-    multiple of 16, the one-site kernel between them and otherwise, for FP32
-    and when forced."""
+    """bench.py's kernel_name mirrors the library's dispatch for 16-bit
+    storage: staged whole rows at most multiples of 8 from 64 to 1024, half
+    rows at 608, 624 and 640, the unstaged pair kernel at every other even
+    length, the one-site kernel at odd lengths, for FP32 and when forced."""
     sys.path.insert(0, ROOT)
     import bench
-    for n in range(8, 1100, 8):
-        stageable = (96 <= n <= 1024 or n == 64) and n % 8 == 0
-        half = 512 < n <= 640 and n % 16 == 0
-        row = stageable and (half or not 512 < n <= 640)
+    for n in list(range(2, 1100, 2)) + [33, 99, 257]:
+        staged = n % 8 == 0 and 64 <= n <= 1024
+        half = n in (608, 624, 640)
+        pair = n % 2 == 0 and (not staged or 64 < n < 104 or 128 < n < 160 or 776 <= n <= 792 or
+                                (512 < n <= 648 and not half))
         for st in ("fp16", "bf16"):
-            assert ("step_row_kernel" in bench.kernel_name(st, "auto", n)) == row, (st, n)
-            assert ("half" in bench.kernel_name(st, "auto", n)) == half, (st, n)
+            name = bench.kernel_name(st, "auto", n)
+            assert ("step_pair_kernel" in name) == pair, (st, n)
+            assert ("half" in name) == half, (st, n)
+            assert ("step_row_kernel" in name) == (n % 2 == 0 and not pair), (st, n)
             assert "step_kernel" in bench.kernel_name(st, "site", n)
         assert bench.kernel_name("fp32", "auto", n).startswith("step_kernel")

@@ -356,22 +356,24 @@ def test_wait_limit_on_half_rows(shape):
     sim.close()
 
 
-@pytest.mark.parametrize("nx,expect", [(456, "row"), (544, "row_half"), (552, "site"), (1000, "row")])
+@pytest.mark.parametrize("nx,expect", [(456, "row"), (544, "pair"), (608, "row_half"), (100, "pair"), (1000, "row"),
+                                        (33, "site")])
 def test_automatic_choice_between_the_tilings(nx, expect):
-    """kernel "auto" is the tiling timed fastest at each row length: whole
-    rows up to 512 sites and above 640, half rows between where nx is a
-    multiple of 16, the one-site kernel where it is not.  The tilings of the
-    row kernel agree bit for bit and differ from the one-site kernel, so
-    auto equals the expected kernel bit for bit and differs from the other
-    kind."""
+    """kernel "auto" is the tiling timed fastest at each row length (whole
+    rows at most multiples of 8 in 64..1024, half rows at 608-640, the
+    unstaged pair kernel at every other even length, the one-site kernel at
+    odd ones).  The row kernel's tilings and the pair kernel agree bit for
+    bit and differ from the one-site kernel, so auto equals the expected
+    kernel bit for bit and differs from the other kind."""
     import torch
     from paper_2212_11024_gb300 import Flame
     shape = (2, 1, nx)
     nz, ny, _ = shape
     u, B = _fields(shape, 63)
-    other = "site" if expect != "site" else "row"
+    # at an odd row length no packed kernel applies: auto is the one-site kernel
+    other = "site" if expect != "site" else None
     pops = {}
-    for k in ("auto", expect, other):
+    for k in ("auto", expect) + ((other,) if other else ()):
         sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0), kernel=k)
         sim.init(None, u, B)
         sim.step(21)
@@ -379,4 +381,85 @@ def test_automatic_choice_between_the_tilings(nx, expect):
         assert sim.sync() is None
         sim.close()
     assert torch.equal(pops["auto"], pops[expect])
-    assert not torch.equal(pops["auto"], pops[other])
+    if other:
+        assert not torch.equal(pops["auto"], pops[other])
+
+
+# The pair kernel: the row kernel's collision on site pairs loaded and
+# stored straight from HBM (any even row length).
+@pytest.mark.parametrize("shape", [(2, 3, 136), (1, 2, 256), (1, 2, 552), (2, 1, 1000)])
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("variant", ["flame", "fd_current"])
+def test_pair_kernel_equals_staged_rows(shape, storage, variant):
+    """Where the staged row kernel also applies, the pair kernel's
+    populations equal it bit for bit after an odd and an even step count."""
+    import torch
+    from paper_2212_11024_gb300 import Flame
+    nz, ny, nx = shape
+    u, B = _fields(shape, 65)
+    sims = [Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage=storage, B_ref=tuple(B0), kernel=k, variant=variant)
+            for k in ("row", "pair")]
+    for s in sims:
+        s.init(None, u, B)
+    for n in (3, 4):
+        for s in sims:
+            s.step(n)
+        assert torch.equal(sims[0].populations(), sims[1].populations())
+    for s in sims:
+        assert s.sync() is None
+        s.close()
+
+
+# row lengths only the pair kernel takes: below 64, not a multiple of 8, a
+# single pair per row (the wrap at both ends of a two-site row)
+PAIR_SHAPES = [(3, 2, 34), (2, 3, 100), (4, 3, 2), (1, 1, 70)]
+
+
+@pytest.mark.parametrize("shape", PAIR_SHAPES)
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_pair_kernel_vs_oracle(shape, storage):
+    """21 steps on the pair kernel against the FP64 oracle at the row
+    kernel's TOL bounds."""
+    u, B = _fields(shape, 67)
+    fg, mg, fo, mo = run_both(shape, 0.52, 0.55, 1.5, u, B, 21, storage=storage, literal=False, Bref=tuple(B0),
+                              kernel="pair")
+    _check_vs_oracle(shape, fg, mg, fo, mo, TOL[storage])
+
+
+@pytest.mark.parametrize("variant", ["bgk", "emhd", "fd_current"])
+def test_pair_kernel_variants_vs_oracle(variant):
+    shape = (2, 3, 34)
+    nz, ny, nx = shape
+    u, B, fg, mg = _variant_run(shape, "fp16", "pair", variant, 21, 69)
+    p = O.Params(nx, ny, nz, 0.52, 0.55, 1.5)
+    fo = O.init(p, None, u, B)
+    O.step_variant(p, fo, 21, variant, literal=False)
+    mo = O.moments(p, fo)
+    _check_vs_oracle(shape, fg, mg, fo, mo, TOL_VARIANT["fp16"])
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 100), (3, 2, 34)])
+def test_pair_kernel_agrees_with_site_kernel(shape):
+    """FP16, 51 steps, pair kernel vs one-site kernel: at most 12 units of the
+    last place apart, and apart somewhere; the pair kernel has no staged
+    copies, so there is no wait to stall (FLAME_ERR_PARAM)."""
+    from paper_2212_11024_gb300 import Flame, FlameError
+    from paper_2212_11024_gb300.flame import FLAME_ERR_PARAM
+    nz, ny, nx = shape
+    u, B = _fields(shape, 71)
+    pops = []
+    for kernel in ("pair", "site"):
+        sim = Flame(nx, ny, nz, 0.52, 0.55, 1.5, storage="fp16", B_ref=tuple(B0), kernel=kernel)
+        sim.init(None, u, B)
+        sim.step(51)
+        pops.append(sim.populations().cpu().numpy())
+        if kernel == "pair":
+            with pytest.raises(FlameError) as e:
+                sim.debug_stall_next_step(256)
+            assert e.value.status == FLAME_ERR_PARAM
+        sim.close()
+    a, b = pops
+    dev = np.abs(b - np.median(b, axis=(1, 2, 3), keepdims=True)).max()
+    d = np.abs(a - b)
+    assert d.max() < 12 * 2.0 ** -11 * dev, d.max() / dev
+    assert (d > 0).any()
