@@ -5,8 +5,9 @@ Workload (default): 256^3 decaying Hall-MHD turbulence -- seeded random-phase
 solenoidal u and B with energy in shells 1..4 (u_rms = b_rms = 0.05, seeds 3
 and 4), rho = 1, tau_nu = tau_eta = 0.51, d_i = 0.05 * 256 = 12.8.  The
 headline is FP16 deviation storage with FP32 collision; FP32 and BF16
-storage are timed in the same run, and FP16 / BF16 once more with the
-one-site kernel forced ("fp16/site") for comparison with the row kernel.  A
+storage are timed in the same run, FP16 / BF16 once more with the one-site
+kernel forced ("fp16/site") for comparison with the row kernel, and FP16
+with the unstaged pair kernel ("fp16/pair", the one other row lengths use).  A
 step is one launch of the fused collide-and-stream kernel over all 256^3
 sites: the row kernel (TMA-staged x rows, two sites per thread in packed
 FP32 pairs) for 16-bit storage, the one-site kernel for FP32.
@@ -92,6 +93,8 @@ def parse_variant(spec):
 
 def kernel_name(storage, kernel, n):
     """The step kernel flame_step launches for this storage at n^3."""
+    if kernel == "pair" and storage in ("fp16", "bf16") and n % 2 == 0:
+        return f"step_pair_kernel<{storage}> (unstaged site pairs, packed FP32 pairs)"
     if kernel == "auto" and storage in ("fp16", "bf16") and n % 2 == 0:
         staged = n % 8 == 0 and 64 <= n <= 1024
         if not staged or 64 < n < 104 or 128 < n < 160 or 776 <= n <= 792 or (512 < n <= 648 and not (
@@ -386,8 +389,9 @@ def main():
                     help="NX,NY,NZ: a non-cubic lattice of the same recipe (d_i = 0.05 NX), e.g. a smaller "
                          "case of the 256-site-row kernel for profiling; default n^3")
     ap.add_argument("--impl", default="flame", choices=["flame", "reference"])
-    ap.add_argument("--storage", default="fp16,fp32,bf16,fp16/site,bf16/site",
-                    help="first entry is the headline; '/site' forces the one-site kernel")
+    ap.add_argument("--storage", default="fp16,fp32,bf16,fp16/site,bf16/site,fp16/pair",
+                    help="first entry is the headline; '/site' forces the one-site kernel, '/pair' the "
+                         "unstaged pair kernel")
     ap.add_argument("--no-turbulence-runs", action="store_true",
                     help="skip the 128^3 and 512^3 decaying-turbulence runs recorded besides the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true",
