@@ -52,12 +52,14 @@ def test_slabs_equal_one_context_site_kernel(shape, nslabs, storage):
     grp.close()
 
 
-@pytest.mark.parametrize("shape,nslabs", [((6, 5, 64), 2), ((5, 3, 128), 3), ((4, 2, 256), 4)])
+@pytest.mark.parametrize("shape,nslabs", [((6, 5, 64), 2), ((5, 3, 128), 3), ((4, 2, 256), 4), ((5, 3, 40), 2),
+                                          ((4, 2, 136), 3)])
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
 @pytest.mark.parametrize("variant", ["flame", "bgk", "emhd"])
 def test_slabs_equal_one_context_row_kernel(shape, nslabs, storage, variant):
-    """The row kernel (TMA-staged rows) on slabs: tiles only over the slab's
-    planes, odd-step rows staged from the ghost planes."""
+    """The row kernel on slabs (TMA-staged rows at 64, 128 and 256 sites, the
+    unstaged pair kernel at 40 and 136): tiles or pairs only over the slab's
+    planes, odd-step rows read from the ghost planes."""
     u, B = _fields(shape, 63)
     one, grp = _pair(shape, nslabs, storage, variant)
     one.init(None, u, B)
