@@ -96,19 +96,30 @@ def test_step_adjoint_matches_autograd(storage, nsteps, shape):
     assert abs(float(ddi[0]) - ref_d) < tol
 
 
-@pytest.mark.parametrize("storage,nsteps", [("fp16", 3), ("fp32", 4)])
-def test_step_adjoint_full_size_sampled_sites(storage, nsteps):
-    """256^3 (the adjoint's benchmark lattice, d_i = 12.8, tau = 0.51), both
-    AA parities: lambda_t at 16 sampled sites (including the lattice's last
-    plane, row and column) against autograd of the torch restatement's
-    collision of that site alone, with lambda_{t+1} gathered from x + c_q.
-    lambda_t at a site depends only on its own state and on that gather, so
-    the full-size launch is checked site by site."""
+@pytest.mark.parametrize("N,storage,nsteps", [(256, "fp16", 3), (256, "fp32", 4), (512, "fp16", 3)])
+def test_step_adjoint_full_size_sampled_sites(N, storage, nsteps):
+    """256^3 (the adjoint's benchmark lattice, d_i = 0.05 N, tau = 0.51), both
+    AA parities, and 512^3 (lambda of more than 2^31 values): lambda_t at 16
+    sampled sites (including the lattice's last plane, row and column)
+    against autograd of the torch restatement's collision of that site
+    alone, with lambda_{t+1} gathered from x + c_q.  lambda_t at a site
+    depends only on its own state and on that gather, so the full-size
+    launch is checked site by site."""
     import torch
     from paper_2212_11024_gb300 import Flame
     from paper_2212_11024_gb300.flame import library
-    N = 256
-    u, B = turbulence((N, N, N), 3, 0.05, shells=(1, 4))
+    if N <= 256:
+        u, B = turbulence((N, N, N), 3, 0.05, shells=(1, 4))
+    else:
+        # Orszag-Tang fields (Sec. 4.4), built on the device in FP32
+        q = torch.arange(N, device="cuda", dtype=torch.float32) * (2 * np.pi / N)
+        X, Y, Z = q.view(1, 1, N), q.view(1, N, 1), q.view(N, 1, 1)
+        full = (N, N, N)
+        u = torch.stack([(-2 * torch.sin(Y)).expand(full), (2 * torch.sin(X)).expand(full),
+                         torch.zeros(full, device="cuda")]) * 0.02
+        B = torch.stack([(-2 * torch.sin(2 * Y) + torch.sin(Z)).expand(full),
+                         (2 * torch.sin(X) + torch.sin(Z)).expand(full),
+                         (torch.sin(X) + torch.sin(Y)).expand(full)]) * (0.8 * 0.02)
     sim = Flame(N, N, N, 0.51, 0.51, 0.05 * N, storage=storage)
     sim.init(None, u, B)
     del u, B
