@@ -92,18 +92,14 @@ def parse_variant(spec):
 
 
 def kernel_name(storage, kernel, n):
-    """The step kernel flame_step launches for this storage at n^3."""
-    if kernel == "pair" and storage in ("fp16", "bf16") and n % 2 == 0:
-        return f"step_pair_kernel<{storage}> (unstaged site pairs, packed FP32 pairs)"
-    if kernel == "auto" and storage in ("fp16", "bf16") and n % 2 == 0:
-        staged = n % 8 == 0 and 64 <= n <= 1024
-        if not staged or 64 < n < 104 or 128 < n < 160 or 776 <= n <= 792 or (512 < n <= 648 and not (
-                n >= 608 and n % 16 == 0)):
-            return f"step_pair_kernel<{storage}> (unstaged site pairs, packed FP32 pairs)"
-        if 512 < n <= 648:
-            return f"step_row_kernel<{storage}> (half x rows staged by bulk copies, packed FP32 pairs)"
-        return f"step_row_kernel<{storage}> (staged x rows, packed FP32 pairs)"
-    return f"step_kernel<{storage}> (one site per thread)"
+    """The step kernel flame_step launches for this storage at n^3 (the
+    library's own choice, flame_step_kernel)."""
+    from paper_2212_11024_gb300 import flame as F
+    p = F.make_params(n, n, n, 0.51, 0.51, 0.05 * n, storage, kernel=kernel)
+    return {"site": f"step_kernel<{storage}> (one site per thread)",
+            "rows": f"step_row_kernel<{storage}> (staged x rows, packed FP32 pairs)",
+            "half_rows": f"step_row_kernel<{storage}> (half x rows staged by bulk copies, packed FP32 pairs)",
+            "pairs": f"step_pair_kernel<{storage}> (unstaged site pairs, packed FP32 pairs)"}[F.step_kernel(p)]
 
 
 def recorded_traffic(storage):

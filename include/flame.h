@@ -270,6 +270,16 @@ flame_status flame_reduce_sums(flame_ctx *ctx, double *h_sums);
  * site count. */
 int flame_reduce_combine(const flame_params *p, const double *h_sums, double *h_scalars);
 
+/* The step kernel flame_step launches for these parameters (with a state
+ * allocated as flame_create requires): FLAME_KERNEL_SITE (one site per
+ * thread), FLAME_KERNEL_ROWS (x rows staged in shared memory, two sites per
+ * thread), FLAME_KERNEL_HALF_ROWS (half rows staged) or FLAME_KERNEL_PAIRS
+ * (site pairs unstaged); the choice flame_params.kernel leaves to the
+ * library, or the one it forces where it applies.  Host only, no GPU
+ * needed.  Returns 0 for invalid parameters. */
+enum { FLAME_KERNEL_SITE = 1, FLAME_KERNEL_ROWS = 2, FLAME_KERNEL_HALF_ROWS = 3, FLAME_KERNEL_PAIRS = 4 };
+int flame_step_kernel(const flame_params *p);
+
 /* The halo exchange of a lattice split along z into slab contexts (halo_z =
  * 1; the paper splits its domain along one direction and exchanges the
  * boundary nodes every step, Sec. 4).  Under the AA pattern only the odd

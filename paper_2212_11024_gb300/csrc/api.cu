@@ -479,6 +479,27 @@ flame_status flame_reduce_sums(flame_ctx* c, double* h) {
   return h[FLAME_SUM_NONFINITE] > 0 ? FLAME_ERR_NONFINITE : FLAME_OK;
 }
 
+int flame_step_kernel(const flame_params* p) {
+  if (check_params(p) != FLAME_OK) return 0;
+  flame::Grid g{};
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz + 2 * p->halo_z;
+  g.n3 = (long long)p->nx * p->ny * g.nz;
+  g.z0 = p->halo_z;
+  g.nzi = p->nz;
+  g.n3i = (long long)p->nx * p->ny * p->nz;
+  // flame_create requires a 256-byte aligned state; only the alignment is
+  // looked at
+  const void* aligned = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
+  if (!flame::step_row_supported(g, p->storage, p->variant, aligned, p->kernel)) return FLAME_KERNEL_SITE;
+  switch (flame::row_segments(g.nx, p->kernel)) {
+    case 0: return FLAME_KERNEL_PAIRS;
+    case 2: return FLAME_KERNEL_HALF_ROWS;
+  }
+  return FLAME_KERNEL_ROWS;
+}
+
 int flame_reduce_combine(const flame_params* p, const double* r, double* h) {
   if (!p || !r || !h || !(r[FLAME_SUM_SITES] > 0)) return -1;
   const double n3 = r[FLAME_SUM_SITES];

@@ -82,6 +82,7 @@ def _lib():
             "flame_state_bytes": (ctypes.c_size_t, [P(Params)]),
             "flame_create": (i, [P(vp), P(Params), vp, vp]),
             "flame_create_fields": (i, [P(vp), P(Params), vp]),
+            "flame_step_kernel": (i, [P(Params)]),
             "flame_init": (i, [vp, vp, vp, vp, vp, vp]),
             "flame_step": (i, [vp, i]),
             "flame_sync": (i, [vp]),
@@ -161,6 +162,18 @@ def reduce_combine(p: Params, sums) -> dict:
     if _lib().flame_reduce_combine(ctypes.byref(p), r, h) != 0:
         raise ValueError("flame_reduce_combine: invalid sums")
     return dict(zip(SCALAR_NAMES, list(h)))
+
+
+STEP_KERNELS = {1: "site", 2: "rows", 3: "half_rows", 4: "pairs"}
+
+
+def step_kernel(p: Params) -> str:
+    """flame_step_kernel: which step kernel flame_step launches for these
+    parameters ("site", "rows", "half_rows" or "pairs"); host only."""
+    k = _lib().flame_step_kernel(ctypes.byref(p))
+    if k == 0:
+        raise FlameError(FLAME_ERR_PARAM, "flame_step_kernel")
+    return STEP_KERNELS[k]
 
 
 def halo_plan(p: Params, parity: int, face: int):

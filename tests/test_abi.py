@@ -121,3 +121,21 @@ def test_units_relaxation_times():
     assert abs(U.tau_from_nu(1.0 / 30) - 0.6) < 1e-15 and abs(U.tau_from_eta(1.0 / 40) - 0.6) < 1e-15
     lp = U.lattice_params(64, 0.05, 100.0, 1.0, 0.05)
     assert abs(lp["nu"] - 0.05 / np.sqrt(3) * 64 / 100) < 1e-15 and abs(lp["d_i"] - 3.2) < 1e-15
+
+
+def test_step_kernel_choice_without_a_gpu(lib):
+    """flame_step_kernel names the kernel flame_step would launch, on the
+    host: the row kernel's tilings for 16-bit storage by row length, the
+    one-site kernel for FP32, odd rows and when forced; 0 for bad
+    parameters."""
+    from paper_2212_11024_gb300 import flame as F
+    L = F.library()
+    bad = F.make_params(4, 4, 4, 0.4, 0.6, 0.0)
+    assert L.flame_step_kernel(ctypes.byref(bad)) == 0
+    want = {(256, "fp16", "auto"): "rows", (512, "bf16", "auto"): "rows", (608, "fp16", "auto"): "half_rows",
+            (100, "fp16", "auto"): "pairs", (34, "bf16", "auto"): "pairs", (33, "fp16", "auto"): "site",
+            (256, "fp32", "auto"): "site", (256, "fp16", "site"): "site", (256, "fp16", "pair"): "pairs",
+            (100, "fp16", "row"): "site", (640, "fp16", "row"): "rows", (512, "fp16", "row_half"): "half_rows",
+            (33, "fp16", "pair"): "site"}
+    for (n, st, k), name in want.items():
+        assert F.step_kernel(F.make_params(n, 8, 8, 0.6, 0.6, 1.0, st, kernel=k)) == name, (n, st, k)

@@ -25,10 +25,11 @@ def test_reference_arm_prints_the_contract_line():
 
 
 def test_bench_names_the_kernel_flame_step_uses():
-    """bench.py's kernel_name mirrors the library's dispatch for 16-bit
-    storage: staged whole rows at most multiples of 8 from 64 to 1024, half
-    rows at 608, 624 and 640, the unstaged pair kernel at every other even
-    length, the one-site kernel at odd lengths, for FP32 and when forced."""
+    """bench.py names the kernel the library chooses (flame_step_kernel),
+    and that choice follows the timed rule for 16-bit storage: staged whole
+    rows at most multiples of 8 from 64 to 1024, half rows at 608, 624 and
+    640, the unstaged pair kernel at every other even length, the one-site
+    kernel at odd lengths, for FP32 and when forced."""
     sys.path.insert(0, ROOT)
     import bench
     for n in list(range(2, 1100, 2)) + [33, 99, 257]:
