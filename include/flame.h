@@ -225,6 +225,36 @@ flame_status flame_moments(flame_ctx *ctx, double *d_rho, double *d_u, double *d
  * [N3], u [3][N3], B [3][N3], J [3][N3], any may be NULL.  Asynchronous. */
 flame_status flame_moments_f32(flame_ctx *ctx, float *d_rho, float *d_u, float *d_B, float *d_J);
 
+/* Host-buffer forms of flame_init_f32 and flame_moments_f32, for a run whose
+ * fields live in host memory.  The fields cross the host link in chunks of z
+ * planes (at most FLAME_IO_CHUNKS, each of whole planes) on a second stream
+ * of the context, each chunk's kernel starting as soon as its data has
+ * arrived (or been written), so that the copies overlap the kernels.  With
+ * page-locked host memory (cudaHostAlloc, cudaHostRegister) the copies are
+ * asynchronous; pageable memory works through the driver's staging, with
+ * less overlap.  The device workspace is the context's field workspace
+ * (6 N3 doubles, allocated on first use and shared with flame_spectra).
+ * Both calls return when the caller's buffers are no longer in use. */
+enum { FLAME_IO_CHUNKS = 32 };
+
+/* flame_init_f32 from host memory: h_rho [N3] (NULL: rho = 1), h_u, h_B
+ * [3][N3] FP32, in flame_init_f32's layout (a z-slab's fields with its
+ * ghost planes); the gradients are the periodic central differences.  The
+ * same initial populations as flame_init_f32 of the same fields, to the bit.
+ * Synchronises (the CFL check).  Errors as flame_init_f32, FLAME_ERR_CUDA for
+ * a failed copy. */
+flame_status flame_init_f32_host(flame_ctx *ctx, const float *h_rho, const float *h_u, const float *h_B);
+
+/* flame_moments_f32 into host memory: h_rho [N3], h_u, h_B, h_J [3][N3]
+ * FP32 of the updated sites, any may be NULL; equal to flame_moments_f32's
+ * fields to the bit.  h_scalars: NULL, or FLAME_NSCALARS entries that
+ * receive flame_reduce's scalars of the same state, computed on the
+ * context's stream while the fields are copied out.  Synchronises.  Errors:
+ * FLAME_ERR_STATE (no flame_init), FLAME_ERR_CUDA, FLAME_ERR_NONFINITE as
+ * flame_reduce (only with h_scalars). */
+flame_status flame_moments_f32_host(flame_ctx *ctx, float *h_rho, float *h_u, float *h_B, float *h_J,
+                                    double *h_scalars);
+
 /* Moments at a list of sites, for time series such as the velocity at a
  * fixed point that Sec. 4.1-4.2 follow: d_sites [nsites] linear site indices
  * (z*ny + y)*nx + x (device), d_out [nsites][10] FP64 (device): rho, u[3],

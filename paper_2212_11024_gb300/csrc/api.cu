@@ -40,7 +40,7 @@ struct flame_ctx {
   unsigned* d_flags;  // [0] non-finite flag, [1] max speed (float bits)
   // internal workspace (lazily allocated)
   double* d_red;      // kRedBlocksMax * kRedVals partials + kRedVals result
-  double* d_fields;   // 6 * N3 doubles (u, B) for spectra
+  double* d_fields;   // 6 * fft_stride(N3) doubles: u, B for spectra; FP32 fields of the host-buffer calls
   void* d_spec;       // nz * ny * (nx/2+1) cufftDoubleComplex
   double* d_shells;   // 2 * nshell_cap doubles
   int nshell_cap;
@@ -55,6 +55,12 @@ struct flame_ctx {
   flame::Grid g;
   unsigned stall_tries;  // > 0: the next flame_step runs the wait-failure test (flame_debug_stall_next_step)
   void* spectral;        // workspace of the spectral diagnostics (spectral.cu), lazily allocated
+  // the host-buffer calls: their copy stream and events, created on first use
+  cudaStream_t io_stream;
+  cudaEvent_t io_ev[flame::kIoChunks + 1];
+  int n_io_ev;  // events created
+  bool has_io_stream;
+  size_t io_max_pitch;  // the device's largest pitch of a 2-D copy, in bytes
 };
 
 namespace {
@@ -267,25 +273,16 @@ flame_status flame_create_fields(flame_ctx** out, const flame_params* p, void* s
 
 }  // extern "C"
 
-// flame_init and flame_init_f32: the fields' element type F (double or float).
-template <class F>
-static flame_status init_from(flame_ctx* c, const F* d_rho, const F* d_u, const F* d_B, const F* d_gradu,
-                              const F* d_gradB) {
-  if (!c) return FLAME_ERR_PARAM;
-  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
-  if (!c->state) return FLAME_ERR_STATE;
-  if (!d_u || !d_B) return FLAME_ERR_PARAM;
+// flame_init, flame_init_f32 and flame_init_f32_host: `launch` queues the
+// initialisation on the context's stream once the flags are cleared; the CFL
+// number then comes from the maximum speed the initialisation recorded.
+template <class Launch>
+static flame_status init_with(flame_ctx* c, Launch&& launch) {
   // a fresh initial state clears a previous non-finite condition
   c->sticky = FLAME_OK;
   c->nonfinite = 0;
   cudaError_t e = cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(unsigned), c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e);
-  if constexpr (sizeof(F) == sizeof(double))
-    e = flame::launch_init(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu, d_gradB,
-                           c->d_flags + 1, c->stream);
-  else
-    e = flame::launch_init_f32(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu,
-                               d_gradB, c->d_flags + 1, c->stream);
+  if (e == cudaSuccess) e = launch();
   if (e != cudaSuccess) return cuda_fail(c, e);
   unsigned bits = 0;
   e = cudaMemcpyAsync(&bits, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
@@ -305,6 +302,24 @@ static flame_status init_from(flame_ctx* c, const F* d_rho, const F* d_u, const 
   }
   if (c->p.strict_cfl && c->cfl > 1.0) return FLAME_ERR_CFL;
   return FLAME_OK;
+}
+
+// flame_init and flame_init_f32: the fields' element type F (double or float).
+template <class F>
+static flame_status init_from(flame_ctx* c, const F* d_rho, const F* d_u, const F* d_B, const F* d_gradu,
+                              const F* d_gradB) {
+  if (!c) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  if (!c->state) return FLAME_ERR_STATE;
+  if (!d_u || !d_B) return FLAME_ERR_PARAM;
+  return init_with(c, [&]() -> cudaError_t {
+    if constexpr (sizeof(F) == sizeof(double))
+      return flame::launch_init(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu,
+                                d_gradB, c->d_flags + 1, c->stream);
+    else
+      return flame::launch_init_f32(c->p.storage, c->state, c->g, c->k, c->p.init_noneq, d_rho, d_u, d_B, d_gradu,
+                                    d_gradB, c->d_flags + 1, c->stream);
+  });
 }
 
 extern "C" {
@@ -469,6 +484,7 @@ static flame_status reduce_raw(flame_ctx* c, double* r) {
   return FLAME_OK;
 }
 
+static_assert(flame::kIoChunks == FLAME_IO_CHUNKS, "the chunk limit the header states");
 static_assert(flame::kRedVals == FLAME_SUM_SITES, "the reduction's partial sums precede the site count");
 
 flame_status flame_reduce_sums(flame_ctx* c, double* h) {
@@ -537,6 +553,197 @@ flame_status flame_reduce(flame_ctx* c, double* h) {
   return r[FLAME_SUM_NONFINITE] > 0 ? FLAME_ERR_NONFINITE : FLAME_OK;
 }
 
+// The field workspace: 6 fft_stride(N3) doubles, allocated on first use.
+static cudaError_t fields_ws(flame_ctx* c) {
+  if (c->d_fields) return cudaSuccess;
+  const cudaError_t e = cudaMalloc(&c->d_fields, 6 * (size_t)flame::fft_stride(c->g.n3) * sizeof(double));
+  if (e != cudaSuccess) c->d_fields = nullptr;
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// Host-buffer calls: the fields move between host and device in chunks of z
+// planes on a second stream, each chunk's kernel running as soon as its data
+// is there, so that the copies over the host link overlap the kernels.
+
+// The copy stream and events, created on first use, and the field workspace.
+static cudaError_t io_ready(flame_ctx* c) {
+  cudaError_t e = fields_ws(c);
+  if (e == cudaSuccess && !c->has_io_stream) {
+    e = cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) c->has_io_stream = true;
+  }
+  while (e == cudaSuccess && c->n_io_ev < flame::kIoChunks + 1) {
+    e = cudaEventCreateWithFlags(&c->io_ev[c->n_io_ev], cudaEventDisableTiming);
+    if (e == cudaSuccess) ++c->n_io_ev;
+  }
+  if (e == cudaSuccess && c->io_max_pitch == 0) {
+    int mp = 0;
+    e = cudaDeviceGetAttribute(&mp, cudaDevAttrMaxPitch, c->device);
+    c->io_max_pitch = e == cudaSuccess && mp > 0 ? (size_t)mp : 0;
+  }
+  return e;
+}
+
+// Elements [off, off + count) of each of ncomp components `stride` apart:
+// one 2-D copy (a row per component) where the stride is within the
+// device's pitch limit -- each copy over the host link carries a fixed
+// cost, so fewer and larger copies move more -- else one copy per component.
+static cudaError_t copy_comps(float* dst, const float* src, int ncomp, long long stride, long long off,
+                              long long count, cudaMemcpyKind kind, cudaStream_t s, size_t max_pitch) {
+  const size_t pitch = (size_t)stride * sizeof(float);
+  if (ncomp > 1 && pitch <= max_pitch)
+    return cudaMemcpy2DAsync(dst + off, pitch, src + off, pitch, (size_t)count * sizeof(float), (size_t)ncomp, kind,
+                             s);
+  for (int a = 0; a < ncomp; ++a) {
+    const cudaError_t e =
+        cudaMemcpyAsync(dst + a * stride + off, src + a * stride + off, (size_t)count * sizeof(float), kind, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// A field of a host-buffer call: its host array, its place in the workspace
+// and its components (`stride` apart in both).
+struct IoField {
+  float* h;
+  float* d;
+  int ncomp;
+};
+
+// Drops the fields without a host array and merges each field that follows
+// the previous one both in host memory and in the workspace into it, so that
+// fields the caller keeps in one array move in one copy.  Returns the count.
+static int io_merge(IoField* f, int n, long long stride) {
+  const auto follows = [stride](const float* p, int ncomp, const float* q) {
+    return reinterpret_cast<uintptr_t>(p) + (uintptr_t)ncomp * (uintptr_t)stride * sizeof(float) ==
+           reinterpret_cast<uintptr_t>(q);
+  };
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!f[i].h) continue;
+    if (m > 0 && follows(f[m - 1].h, f[m - 1].ncomp, f[i].h) && follows(f[m - 1].d, f[m - 1].ncomp, f[i].d)) {
+      f[m - 1].ncomp += f[i].ncomp;
+      continue;
+    }
+    f[m++] = f[i];
+  }
+  return m;
+}
+
+flame_status flame_init_f32_host(flame_ctx* c, const float* h_rho, const float* h_u, const float* h_B) {
+  const Range range("flame_init_f32_host");
+  if (!c) return FLAME_ERR_PARAM;
+  if (c->sticky == FLAME_ERR_CUDA) return c->sticky;
+  if (!c->state) return FLAME_ERR_STATE;
+  if (!h_u || !h_B) return FLAME_ERR_PARAM;
+  const cudaError_t er = io_ready(c);
+  if (er != cudaSuccess) return cuda_fail(c, er);
+  const flame::Grid g = c->g;
+  const long long n3 = g.n3, plane = (long long)g.nx * g.ny;
+  float* d_u = reinterpret_cast<float*>(c->d_fields);
+  float* d_B = d_u + 3 * n3;
+  float* d_rho = h_rho ? d_u + 6 * n3 : nullptr;
+  // the host arrays are only read (the copies run host to device)
+  IoField f[3] = {{const_cast<float*>(h_u), d_u, 3}, {const_cast<float*>(h_B), d_B, 3},
+                  {const_cast<float*>(h_rho), d_rho, 1}};
+  const int nf = io_merge(f, 3, n3);
+  // the planes held are copied in nc chunks, the updated planes initialised in ni
+  const int nc = flame::io_chunk_count(g.nz), ni = flame::io_chunk_count(g.nzi);
+  const flame_status st = init_with(c, [&]() -> cudaError_t {
+    // the copies overwrite the workspace only after the work queued before
+    cudaError_t e = cudaEventRecord(c->io_ev[flame::kIoChunks], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->io_stream, c->io_ev[flame::kIoChunks], 0);
+    int queued = 0;
+    for (int j = 0; j < nc && e == cudaSuccess; ++j) {
+      const int a = flame::io_first(0, g.nz, nc, j), b = flame::io_first(0, g.nz, nc, j + 1);
+      const long long off = a * plane, cnt = (b - a) * plane;
+      for (int k = 0; k < nf && e == cudaSuccess; ++k)
+        e = copy_comps(f[k].d, f[k].h, f[k].ncomp, n3, off, cnt, cudaMemcpyHostToDevice, c->io_stream,
+                       c->io_max_pitch);
+      if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[j], c->io_stream);
+      // every chunk of updated planes whose planes and z neighbours have now arrived
+      for (int i = 0; i < ni && e == cudaSuccess; ++i) {
+        const int ia = flame::io_first(g.z0, g.nzi, ni, i), ib = flame::io_first(g.z0, g.nzi, ni, i + 1);
+        if (flame::io_init_needs(g.nz, nc, ia, ib) != j) continue;
+        flame::Grid sg = g;
+        sg.z0 = ia;
+        sg.nzi = ib - ia;
+        sg.n3i = plane * (ib - ia);
+        e = cudaStreamWaitEvent(c->stream, c->io_ev[j], 0);
+        if (e == cudaSuccess)
+          e = flame::launch_init_f32(c->p.storage, c->state, sg, c->k, c->p.init_noneq, d_rho, d_u, d_B, nullptr,
+                                     nullptr, c->d_flags + 1, c->stream);
+        ++queued;
+      }
+    }
+    if (e == cudaSuccess && queued != ni) e = cudaErrorInvalidValue;
+    return e;
+  });
+  // no copy from the caller's buffers is in flight after the return
+  const cudaError_t es = cudaStreamSynchronize(c->io_stream);
+  if (st == FLAME_OK && es != cudaSuccess) return cuda_fail(c, es);
+  return st;
+}
+
+flame_status flame_moments_f32_host(flame_ctx* c, float* h_rho, float* h_u, float* h_B, float* h_J,
+                                    double* h_scalars) {
+  const Range range("flame_moments_f32_host");
+  const flame_status su = usable(c);
+  if (su != FLAME_OK && su != FLAME_ERR_NONFINITE) return su;
+  if (!c->initialized) return FLAME_ERR_STATE;
+  cudaError_t e = io_ready(c);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  const flame::Grid g = c->g;
+  const long long n3i = g.n3i, plane = (long long)g.nx * g.ny;
+  // the requested fields, one after another in the workspace, components n3i apart
+  float* w = reinterpret_cast<float*>(c->d_fields);
+  float* d_rho = h_rho ? w : nullptr;
+  w += h_rho ? n3i : 0;
+  float* d_u = h_u ? w : nullptr;
+  w += h_u ? 3 * n3i : 0;
+  float* d_B = h_B ? w : nullptr;
+  w += h_B ? 3 * n3i : 0;
+  float* d_J = h_J ? w : nullptr;
+  IoField f[4] = {{h_rho, d_rho, 1}, {h_u, d_u, 3}, {h_B, d_B, 3}, {h_J, d_J, 3}};
+  const int nf = io_merge(f, 4, n3i);
+  const int n = flame::io_chunk_count(g.nzi);
+  for (int j = 0; j < n && e == cudaSuccess; ++j) {
+    const int a = flame::io_first(g.z0, g.nzi, n, j), b = flame::io_first(g.z0, g.nzi, n, j + 1);
+    const long long off = (a - g.z0) * plane;
+    flame::Grid sg = g;
+    sg.z0 = a;
+    sg.nzi = b - a;
+    sg.n3i = plane * (b - a);
+    e = flame::launch_moments_f32(c->p.storage, c->parity, c->state, sg, c->k, d_rho ? d_rho + off : nullptr,
+                                  d_u ? d_u + off : nullptr, d_B ? d_B + off : nullptr, d_J ? d_J + off : nullptr,
+                                  c->stream, n3i);
+    if (e == cudaSuccess) e = cudaEventRecord(c->io_ev[j], c->stream);
+  }
+  for (int j = 0; j < n && e == cudaSuccess; ++j) {
+    const int a = flame::io_first(g.z0, g.nzi, n, j), b = flame::io_first(g.z0, g.nzi, n, j + 1);
+    const long long off = (a - g.z0) * plane, cnt = (b - a) * plane;
+    e = cudaStreamWaitEvent(c->io_stream, c->io_ev[j], 0);
+    for (int k = 0; k < nf && e == cudaSuccess; ++k)
+      e = copy_comps(f[k].h, f[k].d, f[k].ncomp, n3i, off, cnt, cudaMemcpyDeviceToHost, c->io_stream,
+                     c->io_max_pitch);
+  }
+  flame_status st = FLAME_OK;
+  if (e == cudaSuccess && h_scalars) {
+    // the scalars of the same state, on the context's stream while the fields are copied out
+    double r[FLAME_NSUMS];
+    st = reduce_raw(c, r);
+    if (st == FLAME_OK) {
+      flame_reduce_combine(&c->p, r, h_scalars);
+      if (r[FLAME_SUM_NONFINITE] > 0) st = FLAME_ERR_NONFINITE;
+    }
+  }
+  const cudaError_t es = cudaStreamSynchronize(c->io_stream);
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  return st;
+}
+
 // Shell spectra of the state's u, B (d_u = d_B = null) or of given FP64
 // fields [3][N3] each.
 static flame_status spectra_of(flame_ctx* c, int nshell, const double* d_u, const double* d_B, double* h_Eu,
@@ -549,13 +756,8 @@ static flame_status spectra_of(flame_ctx* c, int nshell, const double* d_u, cons
   cudaError_t e;
   const size_t n3 = (size_t)flame::fft_stride(c->g.n3);  // aligned stride between the six fields
   const size_t nc = (size_t)c->g.nz * c->g.ny * (c->g.nx / 2 + 1);
-  if (!c->d_fields) {
-    e = cudaMalloc(&c->d_fields, 6 * n3 * sizeof(double));
-    if (e != cudaSuccess) {
-      c->d_fields = nullptr;
-      return cuda_fail(c, e);
-    }
-  }
+  e = fields_ws(c);
+  if (e != cudaSuccess) return cuda_fail(c, e);
   if (!c->d_spec) {
     e = cudaMalloc(&c->d_spec, nc * sizeof(cufftDoubleComplex));
     if (e != cudaSuccess) {
@@ -791,6 +993,8 @@ void flame_destroy(flame_ctx* c) {
   cudaFree(c->d_adj_ws);
   cudaFree(c->d_bfield);
   flame::spectral_ws_free(c->spectral);
+  for (int j = 0; j < c->n_io_ev; ++j) cudaEventDestroy(c->io_ev[j]);
+  if (c->has_io_stream) cudaStreamDestroy(c->io_stream);
   delete c;
 }
 

@@ -450,8 +450,8 @@ cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const 
 }
 
 cudaError_t launch_moments_f32(int storage, int odd, const void* pop, Grid g, const StepConsts& k, float* rho,
-                               float* u, float* B, float* J, cudaStream_t s) {
-  return moments_any<float>(storage, odd, pop, g, k, rho, u, B, J, 0, s);
+                               float* u, float* B, float* J, cudaStream_t s, long long ostride) {
+  return moments_any<float>(storage, odd, pop, g, k, rho, u, B, J, ostride, s);
 }
 
 cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, const StepConsts& k, double* f,

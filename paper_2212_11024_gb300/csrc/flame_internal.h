@@ -86,7 +86,32 @@ cudaError_t launch_moments(int storage, int odd, const void* pop, Grid g, const 
                            double* u, double* B, double* J, cudaStream_t s, long long ostride = 0);
 // The same, written as FP32 (flame_moments_f32).
 cudaError_t launch_moments_f32(int storage, int odd, const void* pop, Grid g, const StepConsts& k, float* rho,
-                               float* u, float* B, float* J, cudaStream_t s);
+                               float* u, float* B, float* J, cudaStream_t s, long long ostride = 0);
+
+// The chunks of planes the host-buffer calls (flame_init_f32_host,
+// flame_moments_f32_host) move and compute one at a time: np planes from z0
+// in io_chunk_count(np) chunks, chunk j covering planes
+// [io_first(z0, np, n, j), io_first(z0, np, n, j + 1)).
+constexpr int kIoChunks = 32;
+inline int io_chunk_count(int np) { return np < kIoChunks ? np : kIoChunks; }
+inline int io_first(int z0, int np, int n, int j) { return z0 + (int)((long long)np * j / n); }
+// The chunk of planes [0, nz) in n chunks that holds plane q.
+inline int io_chunk_of(int nz, int n, int q) {
+  int j = 0;
+  while (j + 1 < n && io_first(0, nz, n, j + 1) <= q) ++j;
+  return j;
+}
+// The initialisation of planes [a, b) takes central differences along z, so
+// it reads planes a - 1 .. b (periodic over the nz planes held).  With the
+// held planes copied in order in n chunks, it can start once chunk
+// io_init_needs(...) has arrived.
+inline int io_init_needs(int nz, int n, int a, int b) {
+  int m = io_chunk_of(nz, n, b - 1);
+  const int lo = io_chunk_of(nz, n, (a - 1 + nz) % nz), hi = io_chunk_of(nz, n, b % nz);
+  if (lo > m) m = lo;
+  if (hi > m) m = hi;
+  return m;
+}
 
 cudaError_t launch_populations(int storage, int odd, const void* pop, Grid g, const StepConsts& k,
                                double* f, cudaStream_t s);

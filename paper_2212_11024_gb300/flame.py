@@ -24,6 +24,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libflame.so")
 
 FLAME_OK, FLAME_ERR_PARAM, FLAME_ERR_CFL, FLAME_ERR_NONFINITE, FLAME_ERR_CUDA, FLAME_ERR_STATE, FLAME_ERR_TIMEOUT = range(7)
+# chunks of z planes the host-buffer calls use at most (FLAME_IO_CHUNKS)
+IO_CHUNKS = 32
 STORAGE = {"fp32": 1, "fp16": 2, "bf16": 3}
 VARIANT = {"flame": 0, "bgk": 1, "emhd": 2, "fd_current": 3}
 # flame_params.kernel: "auto" uses the row kernel (TMA-staged rows, packed
@@ -104,6 +106,8 @@ def _lib():
             "flame_debug_stall_next_step": (i, [vp, ctypes.c_uint]),
             "flame_init_f32": (i, [vp, vp, vp, vp, vp, vp]),
             "flame_moments_f32": (i, [vp, vp, vp, vp, vp]),
+            "flame_init_f32_host": (i, [vp, vp, vp, vp]),
+            "flame_moments_f32_host": (i, [vp, vp, vp, vp, vp, P(d)]),
             "flame_band_energy": (i, [vp, i, i, vp, P(d), vp, vp]),
             "flame_energy_budget": (i, [vp, i, vp, vp, P(d), P(d), P(d)]),
             "flame_reduce_sums": (i, [vp, P(d)]),
@@ -321,6 +325,62 @@ class Flame:
         rc = fn(self._ctx_or_raise(), self._ptr(r), self._ptr(uu), self._ptr(bb), self._ptr(gu), self._ptr(gb))
         self._after(cur)
         _check(rc, "flame_init_f32" if f32 else "flame_init")
+
+    def _host(self, a, ncomp, shape, what):
+        """A pointer to a C-contiguous FP32 host array (numpy or CPU torch) of
+        shape [ncomp, *shape] (or shape)."""
+        if a is None:
+            return None
+        want = ((ncomp,) + shape) if ncomp else shape
+        if isinstance(a, np.ndarray):
+            ok = a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+            ptr = a.ctypes.data
+        else:
+            ok = a.dtype is self.torch.float32 and a.device.type == "cpu" and a.is_contiguous()
+            ptr = a.data_ptr()
+        if not ok or tuple(a.shape) != want:
+            raise ValueError(f"{what}: expected a C-contiguous FP32 host array of shape {want}")
+        return ctypes.c_void_p(ptr)
+
+    def init_host(self, rho, u, B):
+        """flame_init_f32_host: the initial populations from FP32 fields in
+        host memory (numpy, or CPU torch tensors; page-locked ones, e.g.
+        torch's pin_memory(), let the copies overlap the initialisation):
+        rho [nz,ny,nx] or None, u, B [3,nz,ny,nx] (a z-slab's with its ghost
+        planes).  Returns once the host arrays are no longer in use."""
+        args = (self._host(rho, 0, self.field_shape, "rho"), self._host(u, 3, self.field_shape, "u"),
+                self._host(B, 3, self.field_shape, "B"))
+        cur = self._before()
+        rc = self._lib.flame_init_f32_host(self._ctx_or_raise(), *args)
+        self._after(cur)
+        _check(rc, "flame_init_f32_host")
+
+    def moments_host(self, out=None, scalars=False):
+        """flame_moments_f32_host: rho, u, B, J of the current pre-collision
+        populations (FP32) written into host arrays: `out` a dict of C-contiguous
+        FP32 host arrays (numpy or CPU torch; any key may be absent or None),
+        or None for page-locked torch tensors of all four.  With
+        scalars=True also reduce()'s scalars of the same state, computed
+        while the fields are copied out.  Returns out, or (out, scalars)."""
+        t = self.torch
+        if out is None:
+            out = dict(rho=t.empty(self.shape, dtype=t.float32).pin_memory(),
+                       u=t.empty((3,) + self.shape, dtype=t.float32).pin_memory(),
+                       B=t.empty((3,) + self.shape, dtype=t.float32).pin_memory(),
+                       J=t.empty((3,) + self.shape, dtype=t.float32).pin_memory())
+        ptrs = [self._host(out.get(k), 0 if k == "rho" else 3, self.shape, k) for k in ("rho", "u", "B", "J")]
+        h = (ctypes.c_double * NSCALARS)() if scalars else None
+        cur = self._before()
+        rc = self._lib.flame_moments_f32_host(self._ctx_or_raise(), *ptrs, h)
+        self._after(cur)
+        if not scalars:
+            _check(rc, "flame_moments_f32_host")
+            return out
+        if rc not in (FLAME_OK, FLAME_ERR_NONFINITE):
+            _check(rc, "flame_moments_f32_host")
+        vals = dict(zip(SCALAR_NAMES, list(h)))
+        vals["status"] = rc
+        return out, vals
 
     def step(self, n=1):
         _check(self._lib.flame_step(self._ctx_or_raise(), int(n)), "flame_step")

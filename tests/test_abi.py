@@ -139,3 +139,10 @@ def test_step_kernel_choice_without_a_gpu(lib):
             (33, "fp16", "pair"): "site"}
     for (n, st, k), name in want.items():
         assert F.step_kernel(F.make_params(n, 8, 8, 0.6, 0.6, 1.0, st, kernel=k)) == name, (n, st, k)
+
+
+def test_io_chunk_limit_matches_header():
+    from paper_2212_11024_gb300 import flame as F
+    txt = open(os.path.join(ROOT, "include", "flame.h")).read()
+    m = re.search(r"FLAME_IO_CHUNKS\s*=\s*(\d+)", txt)
+    assert m and int(m.group(1)) == F.IO_CHUNKS
