@@ -395,7 +395,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--n", type=int, default=256)
+    # --lattice: the same, for launches under torchrun, whose own parser takes
+    # "--n" for an ambiguous prefix of its options
+    ap.add_argument("--n", "--lattice", dest="n", type=int, default=256, help="lattice edge (n^3)")
     ap.add_argument("--shape", default=None,
                     help="NX,NY,NZ: a non-cubic lattice of the same recipe (d_i = 0.05 NX), e.g. a smaller "
                          "case of the 256-site-row kernel for profiling; default n^3")

@@ -44,3 +44,22 @@ def test_bench_names_the_kernel_flame_step_uses():
             assert ("step_row_kernel" in name) == (n % 2 == 0 and not pair), (st, n)
             assert "step_kernel" in bench.kernel_name(st, "site", n)
         assert bench.kernel_name("fp32", "auto", n).startswith("step_kernel")
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """Launched as the multi-GPU runs are (torchrun, two ranks), rank 0 alone
+    times the oracle and prints; the other rank exits 0 without work."""
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--lattice", "16", "--steps", "1", "--warmup", "0"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
